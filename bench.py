@@ -1,0 +1,322 @@
+"""Benchmark of the sector product y = H x on the GPU (one JSON line on stdout).
+
+Default workload: the spin-1/2 J1-J2 Heisenberg model on the periodic 6x5 square lattice
+(site = x + 6y; 60 nearest bonds J1 = 1, 60 next-nearest bonds J2 = 0.5), N = 15 up spins,
+D = 155,117,520, split into n_sub = 2 subsystems of 15 sites, FP64 vectors, one right-hand
+side. One step is one full product (row enumeration, diagonal, every hop, rank, gather, store)
+over the whole sector, x drawn from the seeded generator (U[-1,1], normalised).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload j1j2|chain|bose|xxz] [--n-sub K] [--dtype f64|f32] [--nrhs R]
+
+``--impl reference`` times the CPU oracle (plain numpy, as it stands) on a bounded sample of
+rows of the same workload, on this machine's host cores; under torchrun only rank 0 runs it.
+Multi-GPU runs are independent replicas (the product is not sharded): every rank runs the whole
+workload and ``value`` counts the rows of all ranks over the slowest rank's time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "H·v sector elements/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM = 6800.0
+
+# DRAM traffic per launch of the product kernel from one ncu capture, keyed by the SHA-256 of the
+# kernel sources it was taken on; reported only while the sources are unchanged.
+NCU_TRAFFIC = {}
+
+WORKLOADS = {
+    "j1j2": 2,
+    "chain": 1,
+    "bose": 3,
+    "xxz": 5,
+}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_14591_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".h", ".cpp")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"dq_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.dev)], stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [v.strip() for v in line.split(",")]
+                    if len(p) >= 9 and p[1].isdigit():
+                        rows.append(p)
+            os.remove(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [int(r[1]) for r in rows]
+        mx = max(int(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        load = [v for v in sm if v >= 0.5 * mx] or sm
+        return {"sm_mhz": int(statistics.median(load)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
+
+
+def build_workload(number: int, n_sub, D_only=False):
+    from paper_2407_14591_gb300 import binding as b
+    from paper_2407_14591_gb300 import workloads as wl
+
+    w, _ = wl.workload(number, n_sub=n_sub, draw_vector=False)
+    s = b.make_sector(w.L, w.Q, w.N, w.n_sub)
+    w, x = wl.workload(number, n_sub=n_sub, D=s.dim)
+    return w, s, x
+
+
+def oracle_rows_rate(w, partition, x, seconds: float, steps: int | None = None, warmup: int = 0):
+    """Time the oracle's gather form on bounded row samples; returns (rows/s, rows timed, note)."""
+    from oracle import OracleSector, matvec_rows
+
+    t0 = time.perf_counter()
+    o = OracleSector(w.L, w.Q, w.N, partition=partition)
+    setup = time.perf_counter() - t0
+    rng = np.random.default_rng(12345)
+    rows_per = 1 << 12
+    # calibrate the sample size so one step takes about `seconds / steps`
+    t0 = time.perf_counter()
+    matvec_rows(o, w.terms, x, rng.choice(o.dim, rows_per, replace=False))
+    dt = time.perf_counter() - t0
+    n_steps = steps if steps is not None else 4
+    target = seconds / n_steps
+    rows_per = int(min(o.dim, max(1 << 10, rows_per * target / max(dt, 1e-6))))
+    for _ in range(warmup):
+        matvec_rows(o, w.terms, x, rng.choice(o.dim, rows_per, replace=False))
+    done = 0
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        matvec_rows(o, w.terms, x, rng.choice(o.dim, rows_per, replace=False))
+        done += rows_per
+    el = time.perf_counter() - t0
+    return done / el, done, el, setup, rows_per
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    number = WORKLOADS[args.workload]
+    from paper_2407_14591_gb300 import workloads as wl
+    from oracle import OracleSector, most_equal_partition, sector_dim
+
+    w, _ = wl.workload(number, n_sub=args.n_sub, draw_vector=False)
+    part = most_equal_partition(w.L, w.n_sub, w.Q)
+    D = sector_dim(w.L, w.Q, w.N)
+    w, x = wl.workload(number, n_sub=args.n_sub, D=D)
+    rate, done, el, setup, per = oracle_rows_rate(w, part, x, seconds=max(10.0, 2.0 * args.steps), steps=args.steps,
+                                                  warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "elements/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "D": D, "n_sub": w.n_sub, "partition": part, "nrhs": 1},
+        "cpu_baseline": {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{per} random rows per step (gather form), {args.steps} steps, "
+                                   f"after a {setup:.0f} s untimed sector build (enumerate + sort)"},
+        "e2e": {"value": rate, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="j1j2", choices=sorted(WORKLOADS))
+    ap.add_argument("--n-sub", type=int, default=None)
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2407_14591_gb300 import binding as b
+
+    number = WORKLOADS[args.workload]
+    w, s, x_np = build_workload(number, args.n_sub)
+    tdtype = torch.float64 if args.dtype == "f64" else torch.float32
+    esize = 8 if args.dtype == "f64" else 4
+    if args.nrhs > 1:
+        rng = np.random.default_rng(777)
+        x_np = np.repeat(x_np[:, None], args.nrhs, axis=1) * rng.uniform(0.5, 1.5, size=(1, args.nrhs))
+    x = torch.from_numpy(np.ascontiguousarray(x_np)).to("cuda", tdtype)
+    y = torch.empty_like(x)
+    t = b.make_terms(s, w.terms)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        b.matvec(s, t, x, y)
+    torch.cuda.synchronize()
+    s.check_device()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches_per_step = (args.nrhs + 7) // 8
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            b.matvec(s, t, x, y)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    s.check_device()
+    ms_step = ms / args.steps
+    rows = s.dim * args.nrhs
+    value = world * rows * args.steps / (ms / 1e3)
+    alg_bytes = s.dim * args.nrhs * 2 * esize
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    src_hash = kernel_source_hash()
+    traffic = NCU_TRAFFIC.get((w.name, s.n_sub, args.dtype, args.nrhs, src_hash))
+
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.empty(x.shape, dtype=tdtype, pin_memory=True)
+        xh.copy_(x)
+        yh = torch.empty(x.shape, dtype=tdtype, pin_memory=True)
+        k_e2e = max(2, min(args.steps, 10))
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k_e2e):
+            x.copy_(xh, non_blocking=True)
+            b.matvec(s, t, x, y)
+            yh.copy_(y, non_blocking=True)
+        e1.record(stream)
+        barrier()
+        ems = e0.elapsed_time(e1)
+        if dist is not None:
+            tt = torch.tensor([ems], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ems = float(tt.item())
+        e2e = {"value": world * rows * k_e2e / (ems / 1e3), "unit": "elements/s",
+               "h2d_bytes_per_step": int(x.numel() * esize), "d2h_bytes_per_step": int(y.numel() * esize),
+               "steps": k_e2e, "ms_per_step": ems / k_e2e}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline and args.nrhs == 1:
+        rate, done, el, setup, per = oracle_rows_rate(w, s.partition, x_np if x_np.ndim == 1 else x_np[:, 0],
+                                                      seconds=12.0)
+        cpu = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
+               "sample": f"{done} random rows in {el:.1f} s (gather form, numpy single thread), after a "
+                         f"{setup:.0f} s untimed sector build"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": w.name, "D": s.dim, "n_sub": s.n_sub, "partition": s.partition,
+                       "nrhs": args.nrhs, "L2": "inputs larger than L2" if alg_bytes > 129e6 else "inputs fit in L2",
+                       "parallelism": f"replicas{world}" if world > 1 else "single"},
+            "effective_GBps": achieved,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                         "algorithmic_bytes_per_launch": alg_bytes, "kernel": "k_matvec",
+                         "source_hash": src_hash},
+            "clocks": clk.summary(),
+            "gpu_launches": launches_per_step * args.steps,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,164 @@
+/*
+ * dq.h -- C-ABI of the GB300 library for one particle-number (U(1)) sector of a lattice
+ * Hamiltonian: divide-and-conquer basis ranking and the matrix-free product y = H x.
+ *
+ * Source of the method: Schaefer and Luitz, "DanceQ: High-performance library for
+ * number-conserving bases", arXiv:2407.14591.
+ *   - the problem and the three basis functions (i) get_index, (ii) increment, (iii) get_state:
+ *     Sec. 2.1 and Sec. 2.2;
+ *   - the canonical order, Eq. (index), Eq. (ck), Eq. (lambda), Eq. (offset), Eq. (stride):
+ *     Sec. 3.1 and Sec. 3.2; the two limits (Lin's two tables, on-the-fly): Sec. 3.3;
+ *   - the sector dimension D_Q(L, n), Eq. (dim) and App. A;
+ *   - the matrix-free product and Lanczos: Sec. 2.1, Sec. 4.4 and App. D.
+ *
+ * Conventions shared by every call:
+ *   - L sites, local dimension Q (2 <= Q <= 16), Nbits = ceil(log2 Q) bits per site, N particles
+ *     (the paper's n). A basis state is one uint64 word; site i occupies bits
+ *     [Nbits*(L-1-i), Nbits*(L-i)), i.e. site 0 is the most significant digit (Sec. 4.2).
+ *     L * Nbits <= 64.
+ *   - The lattice is split into n_sub consecutive subsystems of most-equal length, the first
+ *     (L mod n_sub) being one site longer (Sec. 4.3). n_sub = 0 selects the paper's default
+ *     ceil(Nbits * L / 16) (Eq. (Nopt_from_L)).
+ *   - The canonical order is that of Sec. 3.2: the last subsystem varies fastest; inside a
+ *     subsystem, states are ordered by their own particle number and then lexicographically
+ *     with the subsystem's first site most significant (Table 1).
+ *   - Every call returns DQ_OK (0) or a negative status; dq_last_error() then describes the
+ *     failure (thread-local). No C++ exception crosses this boundary.
+ *   - Pointers named d_* and the x / y / v0 vectors are DEVICE pointers owned by the caller, on
+ *     the device that was current when the sector was made. Host pointers are named plainly.
+ *   - A `stream` argument is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls that take a stream are asynchronous with respect to the host unless stated.
+ */
+#ifndef DQ_H
+#define DQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define DQ_OK 0
+#define DQ_EINVAL (-1)   /* an argument is out of its documented range                    */
+#define DQ_ERANGE (-2)   /* the sector is too large (D >= 2^63, or a table would not fit)  */
+#define DQ_EINDEX (-3)   /* an index >= D                                                  */
+#define DQ_ESTATE (-4)   /* a word that is not a state of the sector                       */
+#define DQ_ENOMEM (-5)   /* a host or device allocation failed                             */
+#define DQ_ECUDA (-6)    /* a CUDA runtime call failed                                     */
+#define DQ_EDEVICE (-7)  /* a kernel flagged bad input through the sector's error word     */
+
+/* ---- vector element types ------------------------------------------------------------- */
+#define DQ_F64 0 /* vectors stored as double                                         */
+#define DQ_F32 1 /* vectors stored as float; accumulation is exact (fixed point)      */
+
+/* ---- operator term kinds (all Hermitian, real) -------------------------------------------- */
+/* Spin-1/2 (Q = 2 only; a particle is an up spin, Sz = sigma - 1/2; App. D's Hamiltonian):  */
+#define DQ_XY 0  /* coef * 1/2 (S+_i S-_j + S-_i S+_j)                                        */
+#define DQ_ZZ 1  /* coef * Sz_i Sz_j                                                         */
+#define DQ_Z 2   /* coef * Sz_i                     (j ignored)                              */
+/* Bosons, any Q (occupation n = digit, truncated at Q-1):                                   */
+#define DQ_HOP 3 /* -coef * (b+_i b_j + b+_j b_i)                                            */
+#define DQ_NN 4  /* coef * n_i n_j                                                           */
+#define DQ_N 5   /* coef * n_i                      (j ignored)                              */
+#define DQ_U 6   /* coef / 2 * n_i (n_i - 1)        (j ignored)                              */
+
+typedef struct dq_sector dq_sector; /* opaque: partition, tables on host and device          */
+typedef struct dq_terms dq_terms;   /* opaque: compiled operator for one sector               */
+
+typedef struct dq_term {
+    int kind;    /* DQ_XY .. DQ_U                                     */
+    int i, j;    /* sites; j ignored by single-site kinds; i != j     */
+    double coef; /* real coefficient                                  */
+} dq_term;
+
+/* Description of the last failure on the calling thread ("" if none). Never NULL. */
+const char* dq_last_error(void);
+
+/* ---- sector ------------------------------------------------------------------------------ */
+
+/* Build the sector (L, Q, N) split into n_sub subsystems: the D_Q table (Eq. (dim)), the
+ * offset and stride tables (Eq. (offset), Eq. (stride)), one local rank table and one local
+ * unrank list per distinct subsystem length (Sec. 4.2, container (i); filled with the
+ * on-the-fly rank of Alg. 1), and their device copies on the current device.
+ * Arguments: 1 <= L, L*Nbits <= 64, 2 <= Q <= 16, 0 <= N <= (Q-1)L, 0 <= n_sub <= L.
+ * Errors: DQ_EINVAL for out-of-range arguments; DQ_ERANGE if D >= 2^63 or a subsystem is wider
+ * than 24 bits; DQ_ENOMEM / DQ_ECUDA on allocation failure. *out is set only on success and is
+ * owned by the caller (dq_free_sector). Synchronous. */
+int dq_make_sector(int L, int Q, int N, int n_sub, dq_sector** out);
+
+/* Release a sector and its device tables. NULL is allowed. Terms made for it must be freed
+ * first. */
+void dq_free_sector(dq_sector* s);
+
+/* Sector dimension D = D_Q(L, N) (Eq. (dim)). */
+int dq_sector_dim(const dq_sector* s, uint64_t* D);
+
+/* Partition: *n_sub and L_k[0 .. n_sub-1] (caller provides room for 64 ints). */
+int dq_sector_partition(const dq_sector* s, int* n_sub, int* L_k);
+
+/* Function (iii), get_state (Sec. 2.2, Alg. 4), on the host: the state with canonical index
+ * `index`. DQ_EINDEX if index >= D. */
+int dq_state_at(const dq_sector* s, uint64_t index, uint64_t* state);
+
+/* Function (i), get_index (Sec. 2.2, Alg. 2, Eq. (index)), on the host. DQ_ESTATE if `state`
+ * has bits above L*Nbits, a digit >= Q, or a particle number other than N. */
+int dq_index_of(const dq_sector* s, uint64_t state, uint64_t* index);
+
+/* Function (ii), increment (Sec. 2.2, Alg. 3), on the host: the next state in canonical order;
+ * the last state wraps to the first (minimal) one. DQ_ESTATE for an invalid `state`. */
+int dq_next_state(const dq_sector* s, uint64_t state, uint64_t* next);
+
+/* Batched function (iii) on the device: d_state[t] = get_state(d_index[t]) for t < n.
+ * An index >= D writes UINT64_MAX and sets the sector's error word (see dq_check_device).
+ * Asynchronous on `stream`. */
+int dq_state_at_batch(const dq_sector* s, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
+
+/* Batched function (i) on the device: d_index[t] = get_index(d_state[t]) for t < n.
+ * An invalid state writes UINT64_MAX and sets the error word. Asynchronous on `stream`. */
+int dq_index_of_batch(const dq_sector* s, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
+
+/* Synchronise `stream`, read and clear the sector's device error word. Returns DQ_EDEVICE if a
+ * kernel flagged bad input since the last check, DQ_OK otherwise. */
+int dq_check_device(const dq_sector* s, void* stream);
+
+/* ---- operator ---------------------------------------------------------------------------- */
+
+/* Compile `n_terms` terms for sector `s` and upload them. Errors: DQ_EINVAL for an unknown kind,
+ * a site out of range, i == j in a pair term, or a spin-1/2 kind with Q != 2. The same
+ * (i, j) pair may appear in several terms; their contributions add. *out is owned by the caller
+ * (dq_free_terms). Synchronous. */
+int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_terms** out);
+
+/* Release compiled terms. NULL is allowed. */
+void dq_free_terms(dq_terms* t);
+
+/* y = H x for `nrhs` right-hand sides (Sec. 2.1, Sec. 4.4): x and y are device arrays of
+ * D * nrhs elements of `dtype` (DQ_F64 or DQ_F32), row-major with the nrhs values of basis
+ * state i contiguous at [i*nrhs, (i+1)*nrhs). y is overwritten; x and y must not overlap.
+ * 1 <= nrhs <= 64. Every y[i] is written exactly once by one thread (gather form), so there
+ * are no atomics and the result is deterministic. Asynchronous on `stream`.
+ * Errors: DQ_EINVAL (NULL pointers, bad dtype or nrhs, terms of another sector). */
+int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
+
+/* Ground-state energy by Lanczos (Sec. 4.4, App. D): starting from v0 (device, D elements of
+ * `dtype`, normalised inside the call, not modified), run up to `steps` steps of
+ *   w = H v_k; alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1};
+ *   (reorth != 0) re-orthogonalise w against all earlier v by classical Gram-Schmidt, twice;
+ *   beta_k = ||w||; v_{k+1} = w / beta_k.
+ * Dot products and norms accumulate in FP64 whatever `dtype` is; the Lanczos vectors are
+ * stored in `dtype`. E0 is the smallest eigenvalue of the tridiagonal matrix, found on the host
+ * by bisection on its Sturm sequence. The call stops early, without error, when
+ * beta_k < 1e-14 * ||T||; *steps_done then holds the number of steps taken. alpha and beta
+ * (host, room for `steps` doubles each, may be NULL) receive the recurrence coefficients.
+ * The workspace ((steps+1) vectors plus scratch) is allocated and freed by the call.
+ * Synchronous: returns when E0 is known. Errors: DQ_EINVAL, DQ_ENOMEM, DQ_ECUDA. */
+int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0, int steps, int dtype, int reorth,
+               double* E0, double* alpha, double* beta, int* steps_done, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DQ_H */

@@ -1,0 +1,254 @@
+"""Thin ctypes binding of ``libdq.so`` (the C-ABI declared in ``include/dq.h``).
+
+Argument marshalling only: every step of the basis machinery and of the product runs in the
+library (host sector builder in C++, kernels in CUDA). The names follow the C-ABI without the
+``dq_`` prefix. Importing this module loads the library and raises if it has not been built;
+there is no fallback.
+
+Vectors are torch tensors on the CUDA device that was current when the sector was made,
+float64 or float32, contiguous, shape (D,) or (D, nrhs). Calls run on torch's current stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdq.so")
+
+DQ_OK, DQ_EINVAL, DQ_ERANGE, DQ_EINDEX, DQ_ESTATE, DQ_ENOMEM, DQ_ECUDA, DQ_EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+DQ_F64, DQ_F32 = 0, 1
+KINDS = {"XY": 0, "ZZ": 1, "Z": 2, "HOP": 3, "NN": 4, "N": 5, "U": 6}
+
+EXPORTED = (
+    "dq_last_error", "dq_make_sector", "dq_free_sector", "dq_sector_dim", "dq_sector_partition",
+    "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
+    "dq_check_device", "dq_make_terms", "dq_free_terms", "dq_matvec", "dq_lanczos",
+)
+
+
+class DQError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+class _Term(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("i", ctypes.c_int), ("j", ctypes.c_int), ("coef", ctypes.c_double)]
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_2407_14591_gb300.build`")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int
+    P = ctypes.POINTER
+    sig = {
+        "dq_last_error": (ctypes.c_char_p, []),
+        "dq_make_sector": (i32, [i32, i32, i32, i32, P(vp)]),
+        "dq_free_sector": (None, [vp]),
+        "dq_sector_dim": (i32, [vp, P(u64)]),
+        "dq_sector_partition": (i32, [vp, P(i32), P(i32)]),
+        "dq_state_at": (i32, [vp, u64, P(u64)]),
+        "dq_index_of": (i32, [vp, u64, P(u64)]),
+        "dq_next_state": (i32, [vp, u64, P(u64)]),
+        "dq_state_at_batch": (i32, [vp, vp, vp, u64, vp]),
+        "dq_index_of_batch": (i32, [vp, vp, vp, u64, vp]),
+        "dq_check_device": (i32, [vp, vp]),
+        "dq_make_terms": (i32, [vp, P(_Term), i32, P(vp)]),
+        "dq_free_terms": (None, [vp]),
+        "dq_matvec": (i32, [vp, vp, vp, vp, i32, i32, vp]),
+        "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
+                             P(ctypes.c_double), P(i32), vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _check(rc: int):
+    if rc != DQ_OK:
+        raise DQError(rc, _lib.dq_last_error().decode())
+
+
+def _stream_handle(stream=None):
+    import torch
+
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Sector:
+    """A particle-number sector (L, Q, N) split into n_sub subsystems (0 = paper default)."""
+
+    def __init__(self, L: int, Q: int, N: int, n_sub: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib.dq_make_sector(L, Q, N, n_sub, ctypes.byref(h)))
+        self._h = h
+        self.L, self.Q, self.N = L, Q, N
+        D = ctypes.c_uint64()
+        _check(_lib.dq_sector_dim(h, ctypes.byref(D)))
+        self.dim = int(D.value)
+        n = ctypes.c_int()
+        parts = (ctypes.c_int * 64)()
+        _check(_lib.dq_sector_partition(h, ctypes.byref(n), parts))
+        self.partition = [int(parts[k]) for k in range(n.value)]
+        self.n_sub = n.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.dq_free_sector(h)
+            self._h = None
+
+    def state_at(self, index: int) -> int:
+        out = ctypes.c_uint64()
+        _check(_lib.dq_state_at(self._h, ctypes.c_uint64(index), ctypes.byref(out)))
+        return int(out.value)
+
+    def index_of(self, state: int) -> int:
+        out = ctypes.c_uint64()
+        _check(_lib.dq_index_of(self._h, ctypes.c_uint64(state), ctypes.byref(out)))
+        return int(out.value)
+
+    def next_state(self, state: int) -> int:
+        out = ctypes.c_uint64()
+        _check(_lib.dq_next_state(self._h, ctypes.c_uint64(state), ctypes.byref(out)))
+        return int(out.value)
+
+    def state_at_batch(self, index, out=None):
+        """Batched function (iii) on the device; index: int64/uint64 CUDA tensor."""
+        import torch
+
+        idx = index.contiguous()
+        out = torch.empty_like(idx) if out is None else out
+        _check(_lib.dq_state_at_batch(self._h, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      idx.numel(), _stream_handle()))
+        return out
+
+    def index_of_batch(self, states, out=None):
+        """Batched function (i) on the device; states: int64/uint64 CUDA tensor of words."""
+        import torch
+
+        st = states.contiguous()
+        out = torch.empty_like(st) if out is None else out
+        _check(_lib.dq_index_of_batch(self._h, ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                      st.numel(), _stream_handle()))
+        return out
+
+    def check_device(self):
+        _check(_lib.dq_check_device(self._h, _stream_handle()))
+
+
+def make_sector(L: int, Q: int, N: int, n_sub: int = 0) -> Sector:
+    return Sector(L, Q, N, n_sub)
+
+
+def sector_dim(sector: Sector) -> int:
+    return sector.dim
+
+
+def state_at(sector: Sector, index: int) -> int:
+    return sector.state_at(index)
+
+
+def index_of(sector: Sector, state: int) -> int:
+    return sector.index_of(state)
+
+
+def next_state(sector: Sector, state: int) -> int:
+    return sector.next_state(state)
+
+
+class Terms:
+    """Operator terms compiled for one sector; ``terms`` is a list of (kind, i, j, coef)."""
+
+    def __init__(self, sector: Sector, terms):
+        arr = (_Term * max(1, len(terms)))()
+        for q, (kind, i, j, c) in enumerate(terms):
+            k = KINDS[kind] if isinstance(kind, str) else int(kind)
+            arr[q] = _Term(k, int(i), int(j), float(c))
+        h = ctypes.c_void_p()
+        _check(_lib.dq_make_terms(sector.handle, arr, len(terms), ctypes.byref(h)))
+        self._h = h
+        self.sector = sector  # keeps the sector alive while the terms exist
+
+    @property
+    def handle(self):
+        return self._h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.dq_free_terms(h)
+            self._h = None
+
+
+def make_terms(sector: Sector, terms) -> Terms:
+    return Terms(sector, terms)
+
+
+def _dtype_code(t) -> int:
+    import torch
+
+    if t.dtype == torch.float64:
+        return DQ_F64
+    if t.dtype == torch.float32:
+        return DQ_F32
+    raise TypeError("vectors must be float64 or float32")
+
+
+def _check_vec(sector: Sector, t, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.shape[0] != sector.dim or t.dim() not in (1, 2):
+        raise ValueError(f"{name} must have shape (D,) or (D, nrhs) with D = {sector.dim}")
+
+
+def matvec(sector: Sector, terms: Terms, x, y=None):
+    """y = H x on torch's current stream; returns y (allocated if not given)."""
+    import torch
+
+    _check_vec(sector, x, "x")
+    if y is None:
+        y = torch.empty_like(x)
+    _check_vec(sector, y, "y")
+    if y.dtype != x.dtype or y.shape != x.shape:
+        raise ValueError("x and y must have the same dtype and shape")
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    _check(_lib.dq_matvec(sector.handle, terms.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                          _dtype_code(x), nrhs, _stream_handle()))
+    return y
+
+
+def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True) -> dict:
+    """Ground-state energy by Lanczos (synchronous). Returns E0, alpha, beta, steps_done."""
+    _check_vec(sector, v0, "v0")
+    if v0.dim() != 1:
+        raise ValueError("v0 must be one vector")
+    E0 = ctypes.c_double()
+    alpha = (ctypes.c_double * max(1, steps))()
+    beta = (ctypes.c_double * max(1, steps))()
+    done = ctypes.c_int()
+    _check(_lib.dq_lanczos(sector.handle, terms.handle, ctypes.c_void_p(v0.data_ptr()), steps, _dtype_code(v0),
+                           1 if reorth else 0, ctypes.byref(E0), alpha, beta, ctypes.byref(done), _stream_handle()))
+    m = done.value
+    return {"E0": E0.value, "alpha": np.array(alpha[:m]), "beta": np.array(beta[:m]), "steps_done": m}

@@ -1,0 +1,340 @@
+// Device kernels: batched rank / unrank and the general matrix-free product y = H x.
+//
+// rank   = Alg. 2 / Eq. (index): sum over subsystems of offset_k(n_k, lambda_k) + stride_k(n_k,
+//          lambda_k) * index_k(sigma^(k)), the local index read from the subsystem's table.
+// unrank = Alg. 4: per subsystem, the particle number n_k with offset(n_k) <= idx <
+//          offset(n_k + 1), the local index idx / stride, and the reverse table.
+// product: every thread owns rows of y (the paper's workers own consecutive rows, Sec. 2.2),
+//          unranks its row, evaluates the diagonal, applies every off-diagonal term, ranks each
+//          produced state and gathers x at that index: y_i = d_i x_i + sum_j h_ij x_j. Each y_i
+//          is written once by one thread, so no atomics are needed and the result is
+//          deterministic.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "dq_internal.h"
+
+namespace dq {
+
+__device__ __forceinline__ int digit_sum(uint32_t f, int nb) {
+    switch (nb) {
+        case 1: return __popc(f);
+        case 2: return __popc(f & 0x55555555u) + 2 * __popc(f & 0xAAAAAAAAu);
+        case 3: return __popc(f & 0x49249249u) + 2 * __popc(f & 0x92492492u) + 4 * __popc(f & 0x24924924u);
+        default:
+            return __popc(f & 0x11111111u) + 2 * __popc(f & 0x22222222u) + 4 * __popc(f & 0x44444444u) +
+                   8 * __popc(f & 0x88888888u);
+    }
+}
+
+__device__ __forceinline__ uint32_t field_of(const DevSector& S, uint64_t w, int k) {
+    return (uint32_t)((w >> S.shift[k]) & ((1ull << (S.nb * S.Lk[k])) - 1));
+}
+
+// Eq. (index) for a valid state. off_s / str_s may live in shared or global memory.
+__device__ __forceinline__ uint64_t d_rank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t w) {
+    uint64_t idx = 0;
+    int lam = 0;
+    for (int k = 0; k < S.n_sub; ++k) {
+        uint32_t f = field_of(S, w, k);
+        uint32_t li = __ldg(S.rank_tab[S.tab[k]] + f);
+        int n = digit_sum(f, S.nb);
+        int o = S.os_base[k] + lam * S.os_ld[k] + n;
+        idx += off_s[o] + str_s[o] * (uint64_t)li;
+        lam += n;
+    }
+    return idx;
+}
+
+// Lin's two-table form (Sec. 3.3): index = c_0(sigma^(0)) + index_1(sigma^(1)).
+__device__ __forceinline__ uint64_t d_rank_lin2(const DevSector& S, uint64_t w) {
+    uint32_t f0 = (uint32_t)(w >> S.shift[0]);
+    uint32_t f1 = (uint32_t)(w & ((1ull << (S.nb * S.Lk[1])) - 1));
+    return __ldg(S.c0_tab + f0) + (uint64_t)__ldg(S.rank_tab[S.tab[1]] + f1);
+}
+
+// Alg. 4 for idx < D.
+__device__ __forceinline__ uint64_t d_unrank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t idx) {
+    uint64_t w = 0;
+    int lam = 0;
+    for (int k = 0; k < S.n_sub; ++k) {
+        int base = S.os_base[k] + lam * S.os_ld[k];
+        int n;
+        uint64_t li;
+        if (k == S.n_sub - 1) {
+            n = S.N - lam;
+            li = idx;  // offset 0, stride 1 for the last subsystem
+            idx = 0;
+        } else {
+            n = 0;
+            while (n < S.nmax[k] && !(idx < off_s[base + n + 1])) ++n;
+            idx -= off_s[base + n];
+            uint64_t st = str_s[base + n];
+            li = idx / st;
+            idx -= li * st;
+        }
+        int t = S.tab[k];
+        uint32_t pat = __ldg(S.unrank_tab[t] + __ldg(S.sec_start[t] + n) + li);
+        w |= (uint64_t)pat << S.shift[k];
+        lam += n;
+    }
+    return w;
+}
+
+__device__ __forceinline__ bool d_valid(const DevSector& S, uint64_t w) {
+    int bits = S.L * S.nb;
+    if (bits < 64 && (w >> bits) != 0) return false;
+    int n = 0;
+    unsigned m = (1u << S.nb) - 1;
+    for (int i = 0; i < S.L; ++i) {
+        int d = (int)((w >> (S.nb * i)) & m);
+        if (d >= S.Q) return false;
+        n += d;
+    }
+    return n == S.N;
+}
+
+// Stage the offset / stride tables in shared memory when they fit.
+__device__ __forceinline__ void stage_os(const DevSector& S, uint64_t* sm, bool use, const uint64_t*& off_s,
+                                         const uint64_t*& str_s) {
+    if (use) {
+        for (int q = threadIdx.x; q < S.os_total; q += blockDim.x) {
+            sm[q] = S.off[q];
+            sm[S.os_total + q] = S.str[q];
+        }
+        __syncthreads();
+        off_s = sm;
+        str_s = sm + S.os_total;
+    } else {
+        off_s = S.off;
+        str_s = S.str;
+    }
+}
+
+__global__ void k_state_at(DevSector S, const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n,
+                           bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t idx = in[t];
+        if (idx >= S.D) {
+            out[t] = ~0ull;
+            atomicAdd(S.err, 1);
+        } else {
+            out[t] = d_unrank(S, off_s, str_s, idx);
+        }
+    }
+}
+
+__global__ void k_index_of(DevSector S, const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n,
+                           bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t w = in[t];
+        if (!d_valid(S, w)) {
+            out[t] = ~0ull;
+            atomicAdd(S.err, 1);
+        } else {
+            out[t] = d_rank(S, off_s, str_s, w);
+        }
+    }
+}
+
+constexpr int kMaxCh = 8;  // right-hand sides handled per pass
+
+template <typename T>
+__device__ __forceinline__ double ld_as_double(const T* p) {
+    return (double)__ldg(p);
+}
+
+// y = H x, Q = 2 operator in bond-layer form. LIN2 selects the two-table rank.
+template <typename T, bool LIN2>
+__global__ void __launch_bounds__(256) k_matvec_q2(DevSector S, DevTermsQ2 H, const T* __restrict__ x,
+                                                   T* __restrict__ y, int ld, int col0, int ch, bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = d_unrank(S, off_s, str_s, i);
+        double d = H.C;
+        if (H.lin) {
+            uint64_t m = s;
+            while (m) {
+                int p = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                d += H.lin[p];
+            }
+        }
+        for (int l = 0; l < H.nl; ++l) {
+            uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+            if (H.kpos[l] < 0) {
+                d += H.K[l] * (double)__popcll(a);
+            } else {
+                while (a) {
+                    int p = __ffsll((long long)a) - 1;
+                    a &= a - 1;
+                    d += H.pos[H.kpos[l] + p];
+                }
+            }
+        }
+        double acc[kMaxCh];
+        const T* xi = x + i * ld + col0;
+#pragma unroll
+        for (int c = 0; c < kMaxCh; ++c) acc[c] = c < ch ? d * ld_as_double(xi + c) : 0.0;
+        for (int l = 0; l < H.nl; ++l) {
+            uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
+            const uint64_t pm = 1ull | (1ull << H.dist[l]);
+            while (o) {
+                int p = __ffsll((long long)o) - 1;
+                o &= o - 1;
+                uint64_t s2 = s ^ (pm << p);
+                uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
+                double amp = H.apos[l] < 0 ? H.A[l] : H.pos[H.apos[l] + p];
+                const T* xj = x + j * ld + col0;
+#pragma unroll
+                for (int c = 0; c < kMaxCh; ++c)
+                    if (c < ch) acc[c] += amp * ld_as_double(xj + c);
+            }
+        }
+        T* yi = y + i * ld + col0;
+#pragma unroll
+        for (int c = 0; c < kMaxCh; ++c)
+            if (c < ch) yi[c] = (T)acc[c];
+    }
+}
+
+// y = H x, general-Q operator (bosons).
+template <typename T, bool LIN2>
+__global__ void __launch_bounds__(256) k_matvec_qg(DevSector S, DevTermsQG H, const T* __restrict__ x,
+                                                   T* __restrict__ y, int ld, int col0, int ch, bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    const int Q = S.Q;
+    const uint64_t dm = (1ull << S.nb) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t s = d_unrank(S, off_s, str_s, i);
+        double d = H.C;
+        for (int q = 0; q < H.nsite; ++q) {
+            int n = (int)((s >> H.site_sh[q]) & dm);
+            d += H.site_f[q * Q + n];
+        }
+        for (int q = 0; q < H.npair; ++q) {
+            int a = (int)((s >> H.pair_sh[2 * q]) & dm), b = (int)((s >> H.pair_sh[2 * q + 1]) & dm);
+            d += H.pair_K[q] * (double)(a * b);
+        }
+        double acc[kMaxCh];
+        const T* xi = x + i * ld + col0;
+#pragma unroll
+        for (int c = 0; c < kMaxCh; ++c) acc[c] = c < ch ? d * ld_as_double(xi + c) : 0.0;
+        for (int q = 0; q < H.nhop; ++q) {
+            const int sa = H.hop_sh[2 * q], sb = H.hop_sh[2 * q + 1];
+            const double t = H.hop_t[q];
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                const int s_up = dir ? sb : sa, s_dn = dir ? sa : sb;  // b+_up b_dn
+                int nu = (int)((s >> s_up) & dm), nd = (int)((s >> s_dn) & dm);
+                if (nu < Q - 1 && nd > 0) {
+                    uint64_t s2 = s + (1ull << s_up) - (1ull << s_dn);
+                    uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
+                    double amp = -t * H.amp[nu * Q + nd];
+                    const T* xj = x + j * ld + col0;
+#pragma unroll
+                    for (int c = 0; c < kMaxCh; ++c)
+                        if (c < ch) acc[c] += amp * ld_as_double(xj + c);
+                }
+            }
+        }
+        T* yi = y + i * ld + col0;
+#pragma unroll
+        for (int c = 0; c < kMaxCh; ++c)
+            if (c < ch) yi[c] = (T)acc[c];
+    }
+}
+
+static int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+static inline size_t os_bytes(const DevSector& S) { return (size_t)S.os_total * 16; }
+static inline bool os_in_smem(const DevSector& S) { return os_bytes(S) <= 48 * 1024; }
+
+static unsigned grid_for(uint64_t n, int threads, int per_sm) {
+    uint64_t need = (n + threads - 1) / threads;
+    uint64_t cap = (uint64_t)num_sms() * per_sm;
+    return (unsigned)(need < cap ? (need ? need : 1) : cap);
+}
+
+int launch_state_at_batch(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream) {
+    bool sm = os_in_smem(S);
+    k_state_at<<<grid_for(n, 256, 8), 256, sm ? os_bytes(S) : 0, (cudaStream_t)stream>>>(S, d_index, d_state, n, sm);
+    return (int)cudaGetLastError();
+}
+
+int launch_index_of_batch(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream) {
+    bool sm = os_in_smem(S);
+    k_index_of<<<grid_for(n, 256, 8), 256, sm ? os_bytes(S) : 0, (cudaStream_t)stream>>>(S, d_state, d_index, n, sm);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+static int launch_matvec_t(const dq_sector* s, const dq_terms* t, const T* x, T* y, int nrhs, cudaStream_t st) {
+    const DevSector& S = s->dev;
+    bool sm = os_in_smem(S);
+    size_t smb = sm ? os_bytes(S) : 0;
+    bool lin2 = (S.n_sub == 2);
+    unsigned grid = grid_for(S.D, 256, 8);
+    for (int c0 = 0; c0 < nrhs; c0 += kMaxCh) {
+        int ch = nrhs - c0 < kMaxCh ? nrhs - c0 : kMaxCh;
+        if (t->q2) {
+            if (lin2)
+                k_matvec_q2<T, true><<<grid, 256, smb, st>>>(S, t->q2v, x, y, nrhs, c0, ch, sm);
+            else
+                k_matvec_q2<T, false><<<grid, 256, smb, st>>>(S, t->q2v, x, y, nrhs, c0, ch, sm);
+        } else {
+            if (lin2)
+                k_matvec_qg<T, true><<<grid, 256, smb, st>>>(S, t->qgv, x, y, nrhs, c0, ch, sm);
+            else
+                k_matvec_qg<T, false><<<grid, 256, smb, st>>>(S, t->qgv, x, y, nrhs, c0, ch, sm);
+        }
+    }
+    return (int)cudaGetLastError();
+}
+
+int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == DQ_F64) return launch_matvec_t<double>(s, t, (const double*)x, (double*)y, nrhs, st);
+    return launch_matvec_t<float>(s, t, (const float*)x, (float*)y, nrhs, st);
+}
+
+}  // namespace dq
+
+using namespace dq;
+
+extern "C" int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs,
+                         void* stream) {
+    clear_error();
+    if (!s || !t || !x || !y) return set_error(DQ_EINVAL, "NULL argument");
+    if (t->sector != s) return set_error(DQ_EINVAL, "terms were compiled for another sector");
+    if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
+    if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
+    if (nrhs < 1 || nrhs > 64) return set_error(DQ_EINVAL, "nrhs must be in [1, 64]");
+    size_t bytes = (size_t)s->D * nrhs * (dtype == DQ_F64 ? 8 : 4);
+    const char* xb = (const char*)x;
+    char* yb = (char*)y;
+    if (xb < yb + bytes && yb < xb + bytes) return set_error(DQ_EINVAL, "x and y overlap");
+    int e = launch_matvec(s, t, x, y, dtype, nrhs, stream);
+    if (e) return set_error(DQ_ECUDA, "matvec launch: %s", cudaGetErrorString((cudaError_t)e));
+    return DQ_OK;
+}

@@ -1,0 +1,245 @@
+// Compilation of operator terms into the device forms used by the product kernels.
+//
+// Q = 2 (one bit per site, spin-1/2 or hard-core bosons): with sigma_p the bit at position
+// p = L-1-i of site i, every diagonal pair term reduces to a constant, single-site fields, and
+// a coefficient of [sigma_i != sigma_j]:
+//   ZZ:  c (s_i - 1/2)(s_j - 1/2) = c/4 - c/2 [s_i != s_j]
+//   NN:  c s_i s_j               = c/2 s_i + c/2 s_j - c/2 [s_i != s_j]
+// and every off-diagonal pair term flips both bits of a pair with s_i != s_j:
+//   XY:  amplitude c/2;   HOP: amplitude -c   (b+_i b_j on Q = 2 is S+_i S-_j).
+// Bonds are grouped into "layers" of equal bit distance, so that [s_p != s_{p+d}] over a whole
+// layer is ((s ^ (s >> d)) & mask), and the per-bond work of the kernel is a popcount (uniform
+// couplings) or a loop over the set bits (per-bond couplings).
+//
+// General Q (bosons): per-site digit functions f_i(n) from N and U, pair coefficients of
+// n_i n_j from NN, and a list of hops with the amplitude table sqrt((n_a + 1) n_b).
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dq_internal.h"
+
+namespace dq {
+
+static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms* t) {
+    const int L = s->L;
+    double C = 0.0;
+    double lin[64] = {0};
+    std::map<std::pair<int, int>, std::pair<double, double>> pairs;  // (lo, d) -> (K, A)
+    for (int q = 0; q < n; ++q) {
+        const dq_term& u = terms[q];
+        int pi = L - 1 - u.i;
+        int pj = (u.kind == DQ_XY || u.kind == DQ_ZZ || u.kind == DQ_HOP || u.kind == DQ_NN) ? L - 1 - u.j : -1;
+        int lo = pj < 0 ? -1 : (pi < pj ? pi : pj);
+        int d = pj < 0 ? 0 : (pi < pj ? pj - pi : pi - pj);
+        double c = u.coef;
+        switch (u.kind) {
+            case DQ_XY: pairs[{lo, d}].second += 0.5 * c; break;
+            case DQ_HOP: pairs[{lo, d}].second += -c; break;
+            case DQ_ZZ: C += 0.25 * c; pairs[{lo, d}].first += -0.5 * c; break;
+            case DQ_NN:
+                lin[pi] += 0.5 * c;
+                lin[pj] += 0.5 * c;
+                pairs[{lo, d}].first += -0.5 * c;
+                break;
+            case DQ_Z: lin[pi] += c; C += -0.5 * c; break;
+            case DQ_N: lin[pi] += c; break;
+            case DQ_U: break;  // n (n - 1) = 0 when n <= 1
+        }
+    }
+    DevTermsQ2& v = t->q2v;
+    std::memset(&v, 0, sizeof v);
+    bool uniform_lin = true;
+    for (int p = 1; p < L; ++p)
+        if (lin[p] != lin[0]) uniform_lin = false;
+    std::vector<double> pos;  // per-position tables, 64 entries each
+    std::vector<double> lin_host;
+    if (uniform_lin) {
+        C += lin[0] * s->N;  // sum_p lin sigma_p = lin * N on the sector
+    } else {
+        lin_host.assign(lin, lin + 64);
+    }
+    v.C = C;
+    // group by distance
+    std::map<int, std::vector<std::pair<int, std::pair<double, double>>>> byd;
+    for (auto& kv : pairs) byd[kv.first.second].push_back({kv.first.first, kv.second});
+    int nl = 0;
+    int hops = 0;
+    for (auto& kv : byd) {
+        int d = kv.first;
+        auto& lst = kv.second;
+        std::map<std::pair<double, double>, uint64_t> groups;
+        for (auto& e : lst) groups[e.second] |= 1ull << e.first;
+        for (auto& e : lst)
+            if (e.second.second != 0.0) ++hops;
+        if (groups.size() <= 3) {
+            for (auto& g : groups) {
+                if (g.first.first == 0.0 && g.first.second == 0.0) continue;
+                if (nl >= kMaxLayers) return set_error(DQ_EINVAL, "too many bond layers");
+                v.dist[nl] = d;
+                v.dmask[nl] = g.first.first != 0.0 ? g.second : 0;
+                v.omask[nl] = g.first.second != 0.0 ? g.second : 0;
+                v.K[nl] = g.first.first;
+                v.A[nl] = g.first.second;
+                v.kpos[nl] = -1;
+                v.apos[nl] = -1;
+                ++nl;
+            }
+        } else {
+            if (nl >= kMaxLayers) return set_error(DQ_EINVAL, "too many bond layers");
+            v.dist[nl] = d;
+            int kb = (int)pos.size();
+            pos.resize(pos.size() + 64, 0.0);
+            int ab = (int)pos.size();
+            pos.resize(pos.size() + 64, 0.0);
+            for (auto& e : lst) {
+                if (e.second.first != 0.0) {
+                    v.dmask[nl] |= 1ull << e.first;
+                    pos[kb + e.first] = e.second.first;
+                }
+                if (e.second.second != 0.0) {
+                    v.omask[nl] |= 1ull << e.first;
+                    pos[ab + e.first] = e.second.second;
+                }
+            }
+            v.kpos[nl] = kb;
+            v.apos[nl] = ab;
+            ++nl;
+        }
+    }
+    v.nl = nl;
+    t->max_hops = hops;
+    int rc;
+    void* p;
+    if (!lin_host.empty()) {
+        if ((rc = dev_upload(t->dev_allocs, lin_host.data(), 64 * 8, &p))) return rc;
+        v.lin = (const double*)p;
+    }
+    if (!pos.empty()) {
+        if ((rc = dev_upload(t->dev_allocs, pos.data(), pos.size() * 8, &p))) return rc;
+        v.pos = (const double*)p;
+    }
+    return DQ_OK;
+}
+
+static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms* t) {
+    const int L = s->L, Q = s->Q, nb = s->nb;
+    std::vector<std::vector<double>> f(L, std::vector<double>(Q, 0.0));
+    std::map<std::pair<int, int>, double> nn;
+    std::vector<int> hop_sh;
+    std::vector<double> hop_t;
+    for (int q = 0; q < n; ++q) {
+        const dq_term& u = terms[q];
+        switch (u.kind) {
+            case DQ_N:
+                for (int d = 0; d < Q; ++d) f[u.i][d] += u.coef * d;
+                break;
+            case DQ_U:
+                for (int d = 0; d < Q; ++d) f[u.i][d] += 0.5 * u.coef * d * (d - 1);
+                break;
+            case DQ_NN: nn[{u.i < u.j ? u.i : u.j, u.i < u.j ? u.j : u.i}] += u.coef; break;
+            case DQ_HOP:
+                hop_sh.push_back(nb * (L - 1 - u.i));
+                hop_sh.push_back(nb * (L - 1 - u.j));
+                hop_t.push_back(u.coef);
+                break;
+            default: return set_error(DQ_EINVAL, "spin-1/2 term kinds need Q = 2");
+        }
+    }
+    DevTermsQG& v = t->qgv;
+    std::memset(&v, 0, sizeof v);
+    std::vector<int> site_sh;
+    std::vector<double> site_f;
+    for (int i = 0; i < L; ++i) {
+        bool any = false;
+        for (int d = 0; d < Q; ++d)
+            if (f[i][d] != 0.0) any = true;
+        if (!any) continue;
+        site_sh.push_back(nb * (L - 1 - i));
+        for (int d = 0; d < Q; ++d) site_f.push_back(f[i][d]);
+    }
+    std::vector<int> pair_sh;
+    std::vector<double> pair_K;
+    for (auto& kv : nn) {
+        if (kv.second == 0.0) continue;
+        pair_sh.push_back(nb * (L - 1 - kv.first.first));
+        pair_sh.push_back(nb * (L - 1 - kv.first.second));
+        pair_K.push_back(kv.second);
+    }
+    std::vector<double> amp((size_t)Q * Q, 0.0);
+    for (int a = 0; a < Q; ++a)
+        for (int b = 0; b < Q; ++b) amp[(size_t)a * Q + b] = std::sqrt((double)((a + 1) * b));
+    v.C = 0.0;
+    v.nsite = (int)site_sh.size();
+    v.npair = (int)pair_K.size();
+    v.nhop = (int)hop_t.size();
+    t->max_hops = 2 * v.nhop;
+    int rc;
+    void* p;
+    if ((rc = dev_upload(t->dev_allocs, site_sh.data(), site_sh.size() * 4, &p))) return rc;
+    v.site_sh = (const int*)p;
+    if ((rc = dev_upload(t->dev_allocs, site_f.data(), site_f.size() * 8, &p))) return rc;
+    v.site_f = (const double*)p;
+    if ((rc = dev_upload(t->dev_allocs, pair_sh.data(), pair_sh.size() * 4, &p))) return rc;
+    v.pair_sh = (const int*)p;
+    if ((rc = dev_upload(t->dev_allocs, pair_K.data(), pair_K.size() * 8, &p))) return rc;
+    v.pair_K = (const double*)p;
+    if ((rc = dev_upload(t->dev_allocs, hop_sh.data(), hop_sh.size() * 4, &p))) return rc;
+    v.hop_sh = (const int*)p;
+    if ((rc = dev_upload(t->dev_allocs, hop_t.data(), hop_t.size() * 8, &p))) return rc;
+    v.hop_t = (const double*)p;
+    if ((rc = dev_upload(t->dev_allocs, amp.data(), amp.size() * 8, &p))) return rc;
+    v.amp = (const double*)p;
+    return DQ_OK;
+}
+
+}  // namespace dq
+
+using namespace dq;
+
+extern "C" {
+
+int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_terms** out) {
+    clear_error();
+    if (!s || !out || (n_terms > 0 && !terms) || n_terms < 0) return set_error(DQ_EINVAL, "bad argument");
+    *out = nullptr;
+    for (int q = 0; q < n_terms; ++q) {
+        const dq_term& u = terms[q];
+        if (u.kind < DQ_XY || u.kind > DQ_U) return set_error(DQ_EINVAL, "term %d: unknown kind %d", q, u.kind);
+        if (u.i < 0 || u.i >= s->L) return set_error(DQ_EINVAL, "term %d: site i out of range", q);
+        bool pair = u.kind == DQ_XY || u.kind == DQ_ZZ || u.kind == DQ_HOP || u.kind == DQ_NN;
+        if (pair && (u.j < 0 || u.j >= s->L || u.j == u.i))
+            return set_error(DQ_EINVAL, "term %d: pair term needs two distinct sites in range", q);
+        bool spin = u.kind == DQ_XY || u.kind == DQ_ZZ || u.kind == DQ_Z;
+        if (spin && s->Q != 2) return set_error(DQ_EINVAL, "term %d: spin-1/2 kinds need Q = 2", q);
+        if (!std::isfinite(u.coef)) return set_error(DQ_EINVAL, "term %d: coefficient is not finite", q);
+    }
+    dq_terms* t = new (std::nothrow) dq_terms();
+    if (!t) return set_error(DQ_ENOMEM, "host allocation");
+    t->sector = s;
+    t->q2 = (s->Q == 2);
+    int rc;
+    try {
+        rc = t->q2 ? compile_q2(s, terms, n_terms, t) : compile_qg(s, terms, n_terms, t);
+    } catch (...) {
+        rc = set_error(DQ_ENOMEM, "host allocation failed while compiling terms");
+    }
+    if (rc) {
+        for (void* p : t->dev_allocs) cudaFree(p);
+        delete t;
+        return rc;
+    }
+    *out = t;
+    return DQ_OK;
+}
+
+void dq_free_terms(dq_terms* t) {
+    if (!t) return;
+    for (void* p : t->dev_allocs) cudaFree(p);
+    delete t;
+}
+
+}  // extern "C"
