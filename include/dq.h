@@ -131,6 +131,13 @@ int dq_check_device(const dq_sector* s, void* stream);
  * (dq_free_terms). Synchronous. */
 int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_terms** out);
 
+/* Which product kernel dq_matvec uses for these terms with one right-hand side: *path = 1 for the
+ * panel kernel (Q = 2, two subsystems, subsystem P_1 of at most 15 sites, uniform single-site
+ * fields, at most two distinct hop amplitudes and four distinct Sz Sz coefficients, dyadic
+ * coefficients; exact fixed-point sums), 0 for the general kernel (any Q and partition; FP64
+ * sums). Both compute the same y up to rounding. */
+int dq_terms_path(const dq_terms* t, int* path);
+
 /* Release compiled terms. NULL is allowed. */
 void dq_free_terms(dq_terms* t);
 

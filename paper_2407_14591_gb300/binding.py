@@ -26,7 +26,7 @@ KINDS = {"XY": 0, "ZZ": 1, "Z": 2, "HOP": 3, "NN": 4, "N": 5, "U": 6}
 EXPORTED = (
     "dq_last_error", "dq_make_sector", "dq_free_sector", "dq_sector_dim", "dq_sector_partition",
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
-    "dq_check_device", "dq_make_terms", "dq_free_terms", "dq_matvec", "dq_lanczos",
+    "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_lanczos",
 )
 
 
@@ -60,6 +60,7 @@ def _load() -> ctypes.CDLL:
         "dq_check_device": (i32, [vp, vp]),
         "dq_make_terms": (i32, [vp, P(_Term), i32, P(vp)]),
         "dq_free_terms": (None, [vp]),
+        "dq_terms_path": (i32, [vp, P(i32)]),
         "dq_matvec": (i32, [vp, vp, vp, vp, i32, i32, vp]),
         "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
                              P(ctypes.c_double), P(i32), vp]),
@@ -192,6 +193,13 @@ class Terms:
     @property
     def handle(self):
         return self._h
+
+    @property
+    def path(self) -> str:
+        """'panel' or 'general': the product kernel used for one right-hand side."""
+        v = ctypes.c_int()
+        _check(_lib.dq_terms_path(self._h, ctypes.byref(v)))
+        return "panel" if v.value == 1 else "general"
 
     def __del__(self):
         h = getattr(self, "_h", None)

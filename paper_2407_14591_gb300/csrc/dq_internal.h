@@ -68,6 +68,57 @@ struct DevTermsQG {
     const double* amp;     // [Q][Q]: sqrt((n_a + 1) n_b)
 };
 
+// Plan of the panel product (Q = 2, two subsystems, Sec. 3.3): with index = c_0(s0) + index_1(s1),
+// the states sharing one P_0 pattern s0 form a contiguous "panel" of D_2(L_1, N - n_0) rows.
+// Hops inside P_1 stay inside a panel, hops inside P_0 map a panel onto another panel of the same
+// length element by element, and hops across the cut map a panel onto a panel of the
+// neighbouring particle-number block. All coefficients are integer multiples of 2^emin.
+constexpr int kPanelMaxBonds = 64;
+constexpr int kPanelMaxLayers = 16;
+constexpr int kPanelMaxGroups = 16;
+constexpr int kPanelMaxA = 2;  // distinct hop amplitudes
+constexpr int kPanelMaxK = 4;  // distinct [s_i != s_j] coefficients
+constexpr int kPanelMaxList = kPanelMaxBonds + kPanelMaxGroups;
+struct PanelPlan {
+    int L0, L1, N;
+    uint32_t npanels;
+    const uint32_t* panel_s0;     // P_0 pattern of every panel, canonical order
+    const uint64_t* panel_start;  // first global index of every panel
+    const uint64_t* c0;           // c_0 of every P_0 pattern (UINT64_MAX: no panel)
+    const uint16_t* t1rank;       // local index of every P_1 pattern
+    const uint16_t* t1states;     // P_1 patterns grouped by particle number
+    uint32_t t1start[18], t1len[18];
+    // off-diagonal, each list sorted by amplitude class; *_end[k] = end of class k
+    int p0_end[kPanelMaxA];       // P_0-internal pairs (two-bit mask in s0)
+    uint32_t p0_mask[kPanelMaxBonds];
+    int n_p1l;                    // P_1-internal pairs grouped in layers of equal distance d
+    int p1l_d[kPanelMaxLayers], p1l_first[kPanelMaxLayers], p1l_cut[kPanelMaxLayers], p1l_end[kPanelMaxLayers];
+    uint32_t p1b_lobit[kPanelMaxBonds];  // bit of the pair's lower position
+    uint32_t p1b_pm2[kPanelMaxBonds];    // pair mask shifted left by one (byte offset into the rank table)
+    int n_xg;                     // crossing groups: one per site a of P_0
+    uint32_t xg_abit[kPanelMaxGroups];
+    int xg_first[kPanelMaxGroups], xg_cut[kPanelMaxGroups], xg_end[kPanelMaxGroups];  // class 0 in [first, cut)
+    uint32_t xb_bit[kPanelMaxBonds];  // bit of site b in s1
+    // diagonal counts of [s_i != s_j], each list sorted by K class
+    int p0z_end[kPanelMaxK];
+    uint32_t p0z_mask[kPanelMaxBonds];
+    int p1z_end[kPanelMaxK];
+    int p1z_d[kPanelMaxLayers];
+    uint32_t p1z_mask[kPanelMaxLayers];
+    int xz_end[kPanelMaxK];
+    uint32_t xz_abit[kPanelMaxBonds], xz_bbit[kPanelMaxBonds];
+    int nA, nK;
+    long long MC, MK[kPanelMaxK], MA[kPanelMaxA];  // coefficients / 2^emin
+    int emin;
+    int cmax;  // longest panel
+    // per-panel source lists (built on the host): panel p owns entries [list_off[p], list_off[p+1])
+    // = its active P_0 partners (first list_cnt0[p] of class 0, then class 1) and then its valid
+    // crossing partners. Entry: global start index | (crossing group << 48).
+    const uint32_t* list_off;
+    const uint32_t* list_hdr;   // bits 0-7: class-0 P_0 partners, 8-15: class-1, 16-23: crossing
+    const uint64_t* list;
+};
+
 // Host-side tables kept by a sector.
 struct HostTables {
     std::vector<uint64_t> Dq;  // (L+1) x (nmax_total+1), saturated at UINT64_MAX
@@ -97,6 +148,10 @@ struct dq_terms {
     dq::DevTermsQG qgv;
     std::vector<void*> dev_allocs;
     int max_hops;  // upper bound on off-diagonal elements per row
+    bool panel_ok = false;     // the panel product applies (see PanelPlan)
+    dq::PanelPlan pp;
+    void* scratch = nullptr;   // fixed-point copy of x and the exponent word, grown on demand
+    size_t scratch_bytes = 0;
 };
 
 namespace dq {
@@ -114,6 +169,14 @@ uint64_t host_unrank(const dq_sector* s, uint64_t idx);
 int launch_state_at_batch(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
 int launch_index_of_batch(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
 int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
+
+// panel product (dq_panel.cpp / dq_panel.cu)
+int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
+                     const std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>>& pairs, dq_terms* t);
+int launch_panel_matvec(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
+size_t panel_scratch_bytes(const dq_sector* s, int dtype);
+int launch_panel_matvec_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* scratch,
+                           void* stream);
 
 // device memory helpers; without a CUDA device dev_upload returns DQ_OK and a NULL pointer
 bool device_present();

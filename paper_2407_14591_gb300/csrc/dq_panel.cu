@@ -1,0 +1,550 @@
+// Panel product y = H x for Q = 2 and two subsystems (plan in dq_panel.cpp).
+//
+// Arithmetic. FP64 work runs at a small fraction of the integer rate on this GPU, so the sums
+// are exact integer sums: a prepass scales x by 2^F (F from the largest exponent in x) and
+// rounds it to int64 (FP64 input, |X| < 2^56) or int32 (FP32 input, |X| < 2^30); every hop adds
+// an integer; the row result sum_k M_k T_k (coefficients M_k = c_k / 2^emin, integers) is formed
+// in 128-bit integers and rounded once to the output type. The only error is the rounding of
+// x to 2^-F, at most 2^-57 (FP64) or 2^-31 (FP32) of max|x| per term.
+//
+// Data movement. One CTA per panel (all rows with one P_0 pattern s0, contiguous in the
+// canonical order). The panel of x is copied to shared memory with a bulk TMA copy; hops inside
+// P_1 are shared-memory gathers through the P_1 rank table (also in shared memory); hops inside
+// P_0 read the partner panel element by element (coalesced); hops across the cut read the panel
+// s0 ^ bit_a of the neighbouring block, double-buffered in shared memory by bulk copies. Every
+// y element is written once, by one thread.
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "dq_internal.h"
+
+namespace dq {
+
+constexpr int kPT = 1024;  // threads per panel CTA
+constexpr int kEPT = 7;    // rows per thread: panels up to 7168 rows (C(15,7) = 6435)
+constexpr unsigned kWaitLimit = 1u << 22;
+
+template <typename T>
+struct FBits;
+template <>
+struct FBits<double> {
+    using U = unsigned long long;
+    static constexpr int MB = 52, EMASK = 0x7ff, BIAS = 1023;
+};
+template <>
+struct FBits<float> {
+    using U = unsigned int;
+    static constexpr int MB = 23, EMASK = 0xff, BIAS = 127;
+};
+template <typename XT>
+struct XHead;
+template <>
+struct XHead<long long> {
+    static constexpr int HEAD = 56;  // |X| <= 2^56: 64 terms still fit in int64
+};
+template <>
+struct XHead<int> {
+    static constexpr int HEAD = 30;
+};
+
+// Workspace header (first 256 bytes of the scratch area).
+struct WsHeader {
+    int emax;  // largest biased exponent in x
+    int F;     // scale exponent: X = round(x 2^F)
+    int bad;   // x held an Inf or NaN
+};
+
+// ------------------------------------------------------------------ prepass -----------------
+
+template <typename T>
+__global__ void k_exp_max(const T* __restrict__ x, uint64_t n, WsHeader* h) {
+    using U = typename FBits<T>::U;
+    int m = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        U b = reinterpret_cast<const U*>(x)[i];
+        int e = (int)((b >> FBits<T>::MB) & FBits<T>::EMASK);
+        m = max(m, e);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&h->emax, m);
+}
+
+template <typename T, typename XT>
+__global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t n, WsHeader* h) {
+    using U = typename FBits<T>::U;
+    constexpr int MB = FBits<T>::MB, BIAS = FBits<T>::BIAS;
+    const int emax = h->emax;
+    if (emax == FBits<T>::EMASK) {  // Inf or NaN in x
+        if (blockIdx.x == 0 && threadIdx.x == 0) h->bad = 1;
+        return;
+    }
+    // |x| < 2^(emax - BIAS + 1), so X = x 2^F stays below 2^HEAD
+    const int F = XHead<XT>::HEAD - (emax - BIAS + 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) h->F = F;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        U b = reinterpret_cast<const U*>(x)[i];
+        int e = (int)((b >> MB) & FBits<T>::EMASK);
+        unsigned long long m = (unsigned long long)(b & (((U)1 << MB) - 1));
+        int ue;
+        if (e) {
+            m |= 1ull << MB;
+            ue = e - BIAS - MB;
+        } else {
+            ue = 1 - BIAS - MB;
+        }
+        int sh = ue + F;  // X = m 2^sh
+        unsigned long long v;
+        if (sh >= 0)
+            v = m << sh;
+        else if (sh > -62)
+            v = (m + (1ull << (-sh - 1))) >> (-sh);  // round half away from zero
+        else
+            v = 0;
+        long long sv = (b >> (sizeof(U) * 8 - 1)) ? -(long long)v : (long long)v;
+        X[i] = (XT)sv;
+    }
+}
+
+// ------------------------------------------------------------------ 128-bit helpers ---------
+
+struct I128 {
+    long long hi;
+    unsigned long long lo;
+};
+
+__device__ __forceinline__ void mac(I128& a, long long u, long long v) {
+    unsigned long long plo = (unsigned long long)u * (unsigned long long)v;
+    long long phi = __mul64hi(u, v);
+    unsigned long long lo = a.lo + plo;
+    a.hi += phi + (lo < a.lo ? 1 : 0);
+    a.lo = lo;
+}
+
+// Round the integer a * 2^scale to the nearest double / float (ties to even).
+template <typename OUT>
+__device__ __forceinline__ OUT i128_to(I128 a, int scale) {
+    constexpr int P = sizeof(OUT) == 8 ? 53 : 24;  // mantissa bits
+    constexpr int BIAS = sizeof(OUT) == 8 ? 1023 : 127;
+    constexpr int EMAXB = sizeof(OUT) == 8 ? 2047 : 255;
+    bool neg = a.hi < 0;
+    unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0 ? 1ull : 0ull);
+    }
+    if (hi == 0 && lo == 0) return (OUT)0;
+    int lz = hi ? __clzll(hi) : 64 + __clzll(lo);
+    if (lz >= 64) {
+        hi = lo << (lz - 64);
+        lo = 0;
+    } else if (lz > 0) {
+        hi = (hi << lz) | (lo >> (64 - lz));
+        lo <<= lz;
+    }
+    // leading bit at 127 of (hi:lo); keep P bits
+    unsigned long long m = hi >> (64 - P);
+    unsigned long long rest = hi << P;  // bits below the mantissa in hi, left-aligned
+    bool guard = (rest >> 63) & 1ull;
+    bool sticky = ((rest << 1) != 0) || lo != 0;
+    int e2 = (127 - lz) + scale;  // exponent of the leading bit
+    if (guard && (sticky || (m & 1ull))) {
+        ++m;
+        if (m >> P) {
+            m >>= 1;
+            ++e2;
+        }
+    }
+    int be = e2 + BIAS;
+    if (be <= 0) return neg ? -(OUT)0 : (OUT)0;  // below the normal range (not reached for sane x)
+    if (be >= EMAXB) return neg ? -(OUT)INFINITY : (OUT)INFINITY;
+    if (sizeof(OUT) == 8) {
+        unsigned long long bits =
+            ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
+        return (OUT)__longlong_as_double((long long)bits);
+    } else {
+        unsigned int bits = ((unsigned int)neg << 31) | ((unsigned int)be << 23) | (unsigned int)(m & ((1u << 23) - 1));
+        return (OUT)__int_as_float((int)bits);
+    }
+}
+
+// ------------------------------------------------------------------ mbarrier / bulk copy -----
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bulk copy of `bytes` (multiple of 16) from 16-byte aligned global memory into shared memory,
+// completing on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`; false if the limit was reached.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+            : "=r"(done)
+            : "r"(smem_addr(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Copy the panel of `len` elements starting at global index `start` into `buf`; returns the
+// offset of element 0 inside `buf` (the copy starts at the 16-byte boundary below `start`).
+template <typename XT>
+__device__ __forceinline__ int stage(XT* buf, const XT* X, uint64_t start, int len, uint64_t* bar) {
+    constexpr int per16 = 16 / sizeof(XT);
+    uint64_t a0 = start & ~(uint64_t)(per16 - 1);
+    int off = (int)(start - a0);
+    uint32_t bytes = (uint32_t)(((off + len) * sizeof(XT) + 15) & ~(size_t)15);
+    bulk_load(buf, X + a0, bytes, bar);
+    return off;
+}
+
+// ------------------------------------------------------------------ panel kernel -------------
+
+// Shared-memory layout of the panel kernel. The P_1 rank table sits at offset 0 and holds byte
+// offsets (local index * sizeof(XT)), so a gather is two loads with no address arithmetic: the
+// table entry at (s1 ^ pair) * 2 and the panel element at kOwn + entry.
+constexpr int kT1Bytes = 65536;  // 2^15 entries of 2 bytes
+constexpr int kOwn = kT1Bytes;   // the panel's own buffer starts here
+template <typename XT>
+struct PanelSmem {
+    static __host__ __device__ size_t al(size_t b) { return (b + 127) & ~(size_t)127; }
+    static __host__ __device__ size_t buf_bytes(int cap) { return al((size_t)cap * sizeof(XT)); }
+    static __host__ __device__ size_t total(int cap, int nstg) {
+        return kT1Bytes + (size_t)(1 + nstg) * buf_bytes(cap) + 128 + 8 * kPanelMaxList;
+    }
+};
+
+template <typename XT>
+__device__ __forceinline__ long long lds_x(const unsigned char* sm, uint32_t off) {
+    return (long long)*reinterpret_cast<const XT*>(sm + off);
+}
+__device__ __forceinline__ uint32_t lds_u16(const unsigned char* sm, uint32_t off) {
+    return (uint32_t)*reinterpret_cast<const uint16_t*>(sm + off);
+}
+
+// Per-panel values shared by all rows: diagonal counts from P_0 and the bit-plane counters of
+// the Sz Sz bonds across the cut.
+struct PanelDiag {
+    int cnt0[kPanelMaxK];
+    uint32_t w0[kPanelMaxK][3], w1[kPanelMaxK][3];
+};
+
+struct PanelCtx {
+    uint32_t s0;
+    uint64_t start;
+    int n1, C, ncls0, np0, nx;
+};
+
+// All the work of one panel for rows tid + e * kPT, e < E. Rows past the panel hold s = 0: no
+// pair inside P_1 is active for them, cut hops read harmless in-range entries, and they are
+// never stored.
+template <typename XT, typename OUT, int NA, int NSTG, int E>
+__device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restrict__ X, OUT* __restrict__ y,
+                                           unsigned char* smem, uint64_t* bar, const uint64_t* lst, const PanelDiag& dg,
+                                           const PanelCtx& pc, size_t bstride, uint32_t& ph_stg, int scale, int& fail) {
+    const int tid = threadIdx.x;
+    const XT* own = reinterpret_cast<const XT*>(smem + kOwn);
+    uint32_t s2[E];  // P_1 pattern of each row, shifted left by one (rank-table byte offset)
+    long long acc[NA][E];
+    const uint16_t* st = P.t1states + P.t1start[pc.n1];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int c = tid + e * kPT;
+        s2[e] = c < pc.C ? ((uint32_t)__ldg(st + c) << 1) : 0u;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) acc[k][e] = 0;
+    }
+    // hops inside P_0: partner panels element by element (two partners per step for more loads
+    // in flight)
+#pragma unroll
+    for (int k = 0; k < NA; ++k) {
+        const int l0 = k ? pc.ncls0 : 0, l1 = k ? pc.np0 : pc.ncls0;
+        int l = l0;
+        for (; l + 1 < l1; l += 2) {
+            const XT* src = X + lst[l];
+            const XT* src2 = X + lst[l + 1];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                int c = tid + e * kPT;
+                if (c < pc.C) acc[k][e] += (long long)__ldg(src + c) + (long long)__ldg(src2 + c);
+            }
+        }
+        if (l < l1) {
+            const XT* src = X + lst[l];
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                int c = tid + e * kPT;
+                if (c < pc.C) acc[k][e] += (long long)__ldg(src + c);
+            }
+        }
+    }
+    // hops inside P_1, layer by layer: a = s ^ (s >> d) marks the active pairs of the layer
+    for (int l = 0; l < P.n_p1l; ++l) {
+        const int d = P.p1l_d[l];
+        uint32_t a[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) a[e] = s2[e] ^ (s2[e] >> d);
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const int q0 = k ? P.p1l_cut[l] : P.p1l_first[l], q1 = k ? P.p1l_end[l] : P.p1l_cut[l];
+            for (int q = q0; q < q1; ++q) {
+                const uint32_t lb = P.p1b_lobit[q] << 1, pm2 = P.p1b_pm2[q];
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (a[e] & lb) acc[k][e] += lds_x<XT>(smem + kOwn, lds_u16(smem, s2[e] ^ pm2));
+            }
+        }
+    }
+    // hops across the cut: panel s0 ^ bit_a of the neighbouring block, NSTG copies in flight
+    for (int j = 0; j < pc.nx; ++j) {
+        const int b = j % NSTG;
+        if (!bar_wait(&bar[1 + b], (ph_stg >> b) & 1u)) fail = 1;
+        ph_stg ^= 1u << b;
+        const uint64_t ent = lst[pc.np0 + j];
+        const int g = (int)(ent >> 48);
+        const unsigned char* sp = smem + kOwn + (1 + b) * bstride + (ent & (16 / sizeof(XT) - 1)) * sizeof(XT);
+        // a hop needs s_b != s_a: with s_a = 1 the particle moves a -> b (b empty)
+        const uint32_t flip = (pc.s0 & P.xg_abit[g]) ? ~0u : 0u;
+        uint32_t sx[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) sx[e] = s2[e] ^ flip;
+#pragma unroll
+        for (int k = 0; k < NA; ++k) {
+            const int b0 = k ? P.xg_cut[g] : P.xg_first[g];
+            const int b1 = k ? P.xg_end[g] : P.xg_cut[g];
+            for (int q = b0; q < b1; ++q) {
+                const uint32_t bb2 = P.xb_bit[q] << 1;
+#pragma unroll
+                for (int e = 0; e < E; ++e)
+                    if (sx[e] & bb2) acc[k][e] += lds_x<XT>(sp, lds_u16(smem, s2[e] ^ bb2));
+            }
+        }
+        __syncthreads();  // buffer b is free again
+        if (tid == 0 && j + NSTG < pc.nx) {
+            const uint64_t e2 = lst[pc.np0 + j + NSTG];
+            const int g2 = (int)(e2 >> 48);
+            const int len = (int)P.t1len[pc.n1 + ((pc.s0 & P.xg_abit[g2]) ? 1 : -1)];
+            stage(reinterpret_cast<XT*>(smem + kOwn + (1 + b) * bstride), X, e2 & ((1ull << 48) - 1), len, &bar[1 + b]);
+        }
+    }
+    // the row result: (C + sum_k K_k n_k) x_i + sum_k A_k S_k, exactly, rounded once
+    const uint32_t m1 = (1u << P.L1) - 1u;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        int c = tid + e * kPT;
+        if (c >= pc.C) continue;
+        const uint32_t s = s2[e] >> 1;
+        long long md = P.MC;
+#pragma unroll
+        for (int k = 0; k < kPanelMaxK; ++k) {
+            if (k >= P.nK) break;
+            long long n = dg.cnt0[k];
+            for (int l = (k ? P.p1z_end[k - 1] : 0); l < P.p1z_end[k]; ++l)
+                n += __popc((s ^ (s >> P.p1z_d[l])) & P.p1z_mask[l]);
+#pragma unroll
+            for (int q = 0; q < 3; ++q) n += (long long)(__popc(s & dg.w0[k][q]) + __popc(~s & m1 & dg.w1[k][q])) << q;
+            md += P.MK[k] * n;
+        }
+        I128 r = {0, 0};
+        mac(r, md, (long long)own[c]);
+#pragma unroll
+        for (int k = 0; k < NA; ++k) mac(r, P.MA[k], acc[k][e]);
+        y[pc.start + c] = i128_to<OUT>(r, scale);
+    }
+}
+
+template <typename XT, typename OUT, int NA, int NSTG>
+__global__ void __launch_bounds__(kPT, 1)
+    k_panel(PanelPlan P, const XT* __restrict__ X, OUT* __restrict__ y, const WsHeader* __restrict__ h, int* err,
+            int cap) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    using SL = PanelSmem<XT>;
+    const int tid = threadIdx.x;
+    uint16_t* t1 = reinterpret_cast<uint16_t*>(smem);
+    XT* own = reinterpret_cast<XT*>(smem + kOwn);
+    const size_t bstride = SL::buf_bytes(cap);
+    unsigned char* tail = smem + kOwn + (size_t)(1 + NSTG) * bstride;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tail);  // [1 + b]: staging buffer b
+    uint64_t* lst = reinterpret_cast<uint64_t*>(tail + 128);
+    __shared__ uint32_t s_hdr;
+    __shared__ int s_fail;
+    __shared__ PanelDiag dg;
+
+    for (int q = tid; q < (1 << P.L1); q += kPT) t1[q] = (uint16_t)(P.t1rank[q] * sizeof(XT));
+    if (tid == 0) {
+        for (int b = 1; b <= NSTG; ++b) bar_init(&bar[b]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_fail = 0;
+    }
+    __syncthreads();
+    if (h->bad) {  // non-finite x: y is left unwritten and the error word is raised
+        if (blockIdx.x == 0 && tid == 0) atomicAdd(err, 1);
+        return;
+    }
+    const int scale = P.emin - h->F;
+    uint32_t ph_stg = 0u;  // mbarrier parity of each staging buffer (bit b)
+    int fail = 0;
+
+    for (uint32_t pi = blockIdx.x; pi < P.npanels; pi += gridDim.x) {
+        PanelCtx pc;
+        pc.s0 = P.panel_s0[pi];
+        pc.start = P.panel_start[pi];
+        pc.n1 = P.N - __popc(pc.s0);
+        pc.C = (int)P.t1len[pc.n1];
+        // warp 0: source list into shared memory and the first copies; warp 1: diagonal counters
+        if (tid < 32) {
+            const uint32_t lo = __ldg(P.list_off + pi), hi = __ldg(P.list_off + pi + 1);
+            for (uint32_t q = lo + tid; q < hi; q += 32) lst[q - lo] = __ldg(P.list + q);
+            if (tid == 0) s_hdr = __ldg(P.list_hdr + pi);
+            __syncwarp();
+            if (tid == 0) {
+                const uint32_t hd = s_hdr;
+                const int np0 = (int)(hd & 255u) + (int)((hd >> 8) & 255u), nx = (int)((hd >> 16) & 255u);
+                for (int j = 0; j < nx && j < NSTG; ++j) {
+                    const uint64_t ent = lst[np0 + j];
+                    const int g = (int)(ent >> 48);
+                    const int len = (int)P.t1len[pc.n1 + ((pc.s0 & P.xg_abit[g]) ? 1 : -1)];
+                    stage(reinterpret_cast<XT*>(smem + kOwn + (1 + j) * bstride), X, ent & ((1ull << 48) - 1), len,
+                          &bar[1 + j]);
+                }
+            }
+        } else if (tid < 32 + kPanelMaxK) {
+            const int k = tid - 32;
+            int c0 = 0;
+            uint32_t w0[3] = {0u, 0u, 0u}, w1[3] = {0u, 0u, 0u};
+            if (k < P.nK) {
+                for (int l = (k ? P.p0z_end[k - 1] : 0); l < P.p0z_end[k]; ++l) c0 += (__popc(pc.s0 & P.p0z_mask[l]) == 1);
+                for (int l = (k ? P.xz_end[k - 1] : 0); l < P.xz_end[k]; ++l) {
+                    // [s_a != s_b]: with s_a = 0 it counts b occupied (w0), with s_a = 1 b empty (w1);
+                    // each is a 3-bit counter per position b, kept as bit planes
+                    const uint32_t bb = P.xz_bbit[l];
+                    const bool one = (pc.s0 & P.xz_abit[l]) != 0;
+                    uint32_t c = one ? 0u : bb, c1 = one ? bb : 0u;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        uint32_t t = w0[q] & c;
+                        w0[q] ^= c;
+                        c = t;
+                        uint32_t tb = w1[q] & c1;
+                        w1[q] ^= c1;
+                        c1 = tb;
+                    }
+                }
+            }
+            dg.cnt0[k] = c0;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                dg.w0[k][q] = w0[q];
+                dg.w1[k][q] = w1[q];
+            }
+        }
+        // the panel's own x: plain coalesced loads into its buffer (element c at kOwn + c*size)
+        {
+            const XT* src = X + pc.start;
+            for (int c = tid; c < pc.C; c += kPT) own[c] = __ldg(src + c);
+        }
+        __syncthreads();
+        const uint32_t hd = s_hdr;
+        pc.ncls0 = (int)(hd & 255u);
+        pc.np0 = pc.ncls0 + (int)((hd >> 8) & 255u);
+        pc.nx = (int)((hd >> 16) & 255u);
+        const int ne = (pc.C + kPT - 1) / kPT;
+        if (ne > 4)
+            panel_rows<XT, OUT, NA, NSTG, 7>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+        else if (ne > 2)
+            panel_rows<XT, OUT, NA, NSTG, 4>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+        else if (ne == 2)
+            panel_rows<XT, OUT, NA, NSTG, 2>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+        else
+            panel_rows<XT, OUT, NA, NSTG, 1>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+        __syncthreads();
+    }
+    if (fail) s_fail = 1;
+    __syncthreads();
+    if (tid == 0 && s_fail) atomicAdd(err, 1);
+}
+
+// ------------------------------------------------------------------ launch -------------------
+
+size_t panel_scratch_bytes(const dq_sector* s, int dtype) {
+    size_t es = dtype == DQ_F64 ? 8 : 4;
+    return 256 + ((size_t)(s->D + 8) * es + 255) / 256 * 256;
+}
+
+static int sms_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+template <typename T, typename XT, int NA, int NSTG>
+static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {
+    const PanelPlan& P = t->pp;
+    WsHeader* h = reinterpret_cast<WsHeader*>(ws);
+    XT* X = reinterpret_cast<XT*>(reinterpret_cast<char*>(ws) + 256);
+    cudaMemsetAsync(h, 0, sizeof(WsHeader), st);
+    const int sms = sms_count();
+    k_exp_max<T><<<sms * 4, 256, 0, st>>>(x, s->D, h);
+    k_to_fixed<T, XT><<<sms * 8, 256, 0, st>>>(x, X, s->D, h);
+    const int cap = P.cmax + 16 / (int)sizeof(XT) + 4;
+    size_t sm = PanelSmem<XT>::total(cap, NSTG);
+    auto kern = k_panel<XT, T, NA, NSTG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return (int)e;
+    unsigned grid = (unsigned)(P.npanels < (uint32_t)sms ? P.npanels : (uint32_t)sms);
+    kern<<<grid, kPT, sm, st>>>(P, X, y, h, s->dev.err, cap);
+    return (int)cudaGetLastError();
+}
+
+template <typename T, typename XT, int NA>
+static int run_panel_n(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {
+    // staging depth that fits next to the rank table and the panel's own buffer (227 KB)
+    return run_panel<T, XT, NA, sizeof(XT) == 8 ? 2 : 5>(s, t, x, y, ws, st);
+}
+
+int launch_panel_matvec_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,
+                           void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const int na = t->pp.nA;
+    if (dtype == DQ_F64) {
+        if (na <= 1) return run_panel_n<double, long long, 1>(s, t, (const double*)x, (double*)y, ws, st);
+        return run_panel_n<double, long long, 2>(s, t, (const double*)x, (double*)y, ws, st);
+    }
+    if (na <= 1) return run_panel_n<float, int, 1>(s, t, (const float*)x, (float*)y, ws, st);
+    return run_panel_n<float, int, 2>(s, t, (const float*)x, (float*)y, ws, st);
+}
+
+int launch_panel_matvec(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream) {
+    size_t need = panel_scratch_bytes(s, dtype);
+    if (t->scratch_bytes < need) {
+        if (t->scratch) cudaFree(t->scratch);
+        t->scratch = nullptr;
+        t->scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&t->scratch, need);
+        if (e != cudaSuccess) return (int)e;
+        t->scratch_bytes = need;
+    }
+    return launch_panel_matvec_ws(s, t, x, y, dtype, t->scratch, stream);
+}
+
+}  // namespace dq

@@ -112,6 +112,11 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     }
     v.nl = nl;
     t->max_hops = hops;
+    {
+        std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>> plist(pairs.begin(), pairs.end());
+        int rc = build_panel_plan(s, C, uniform_lin, plist, t);
+        if (rc) return rc;
+    }
     int rc;
     void* p;
     if (!lin_host.empty()) {
@@ -236,8 +241,16 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
     return DQ_OK;
 }
 
+int dq_terms_path(const dq_terms* t, int* path) {
+    clear_error();
+    if (!t || !path) return set_error(DQ_EINVAL, "NULL argument");
+    *path = t->panel_ok ? 1 : 0;
+    return DQ_OK;
+}
+
 void dq_free_terms(dq_terms* t) {
     if (!t) return;
+    if (t->scratch) cudaFree(t->scratch);
     for (void* p : t->dev_allocs) cudaFree(p);
     delete t;
 }
