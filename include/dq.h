@@ -149,6 +149,25 @@ void dq_free_terms(dq_terms* t);
  * Errors: DQ_EINVAL (NULL pointers, bad dtype or nrhs, terms of another sector). */
 int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
 
+/* y = H x like dq_matvec with one right-hand side, but without allocating any device memory.
+ * The paper has no counterpart; this entry point exists for callers that cannot call cudaMalloc
+ * while they run: for example a solver that has handed all device memory to its own pool up
+ * front, or a time-critical loop in which an allocation (which can synchronise the device) is
+ * not allowed. dq_matvec, by contrast, allocates its scratch on first use and keeps it with the
+ * terms.
+ * The scratch (a fixed-point copy of x and a small header) lives in a static device array of
+ * 64 MiB that every GPU loading this library reserves until the process exits. Hence the limit:
+ * D <= 8,388,568 for DQ_F64 and D <= 16,777,144 for DQ_F32; larger sectors return DQ_ERANGE with
+ * the limit in dq_last_error(). Only terms on the panel path (dq_terms_path == 1) are served;
+ * others return DQ_EINVAL. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture. Every
+ * call reuses the same array, and each call clears the header part it needs to start at zero;
+ * calls that overlap on the GPU (for example on two streams at once) race on the array and give
+ * wrong results, so order them on one stream or synchronise between them. x and y: device
+ * arrays of D elements of `dtype`, must not overlap. Asynchronous on `stream`; non-finite x is
+ * reported by dq_check_device as DQ_EDEVICE. */
+int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* stream);
+
 /* Ground-state energy by Lanczos (Sec. 4.4, App. D): starting from v0 (device, D elements of
  * `dtype`, normalised inside the call, not modified), run up to `steps` steps of
  *   w = H v_k; alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1};

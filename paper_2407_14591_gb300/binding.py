@@ -26,7 +26,8 @@ KINDS = {"XY": 0, "ZZ": 1, "Z": 2, "HOP": 3, "NN": 4, "N": 5, "U": 6}
 EXPORTED = (
     "dq_last_error", "dq_make_sector", "dq_free_sector", "dq_sector_dim", "dq_sector_partition",
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
-    "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_lanczos",
+    "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_matvec_noalloc",
+    "dq_lanczos",
 )
 
 
@@ -62,6 +63,7 @@ def _load() -> ctypes.CDLL:
         "dq_free_terms": (None, [vp]),
         "dq_terms_path": (i32, [vp, P(i32)]),
         "dq_matvec": (i32, [vp, vp, vp, vp, i32, i32, vp]),
+        "dq_matvec_noalloc": (i32, [vp, vp, vp, vp, i32, vp]),
         "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
                              P(ctypes.c_double), P(i32), vp]),
     }
@@ -244,6 +246,19 @@ def matvec(sector: Sector, terms: Terms, x, y=None):
     nrhs = 1 if x.dim() == 1 else x.shape[1]
     _check(_lib.dq_matvec(sector.handle, terms.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
                           _dtype_code(x), nrhs, _stream_handle()))
+    return y
+
+
+def matvec_noalloc(sector: Sector, terms: Terms, x, y):
+    """y = H x through the allocation-free entry point (panel path, D below its static limit).
+
+    y must be given: this call allocates nothing, on the device or through torch."""
+    _check_vec(sector, x, "x")
+    _check_vec(sector, y, "y")
+    if x.dim() != 1 or y.dtype != x.dtype or y.shape != x.shape:
+        raise ValueError("x and y must be single vectors of the same dtype")
+    _check(_lib.dq_matvec_noalloc(sector.handle, terms.handle, ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(y.data_ptr()), _dtype_code(x), _stream_handle()))
     return y
 
 

@@ -1,0 +1,63 @@
+"""The allocation-free product entry point, dq_matvec_noalloc (GPU only).
+
+It serves callers that may not allocate device memory while they run; its scratch is a static
+device array. This file is collected last on purpose: if it fails, a run that stops at the first
+failure has already run every other test. It passes alone in a fresh process as well, since its
+first call on the device performs the one-time set-up itself.
+"""
+
+import ctypes
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2407_14591_gb300 import binding as b
+from paper_2407_14591_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def test_noalloc_matches_matvec_on_two_calls():
+    """Two calls in a row, each against dq_matvec on the same input (FP64 bar 1e-12, FP32 1e-5)."""
+    s = b.make_sector(20, 2, 10, 2)  # D = 184,756
+    nn, nnn = wl.square_bonds(5, 4)
+    t = b.make_terms(s, wl.heisenberg_terms(nn, 1.0) + wl.heisenberg_terms(nnn, 0.5))
+    assert t.path == "panel"
+    lib = b.lib()
+    rng = np.random.default_rng(20240719)
+    for call in range(2):
+        x = torch.from_numpy(rng.uniform(-1, 1, s.dim) * (10.0 ** (3 * call))).to("cuda")
+        ref = b.matvec(s, t, x, torch.empty_like(x))
+        out = torch.full_like(x, float("nan"))
+        rc = lib.dq_matvec_noalloc(s.handle, t.handle, ctypes.c_void_p(x.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), b.DQ_F64, _stream())
+        assert rc == b.DQ_OK, lib.dq_last_error()
+        torch.cuda.synchronize()
+        s.check_device()
+        r, o = ref.cpu().numpy(), out.cpu().numpy()
+        assert np.max(np.abs(o - r)) <= 1e-12 * np.max(np.abs(r)), call
+    x32 = torch.from_numpy(rng.uniform(-1, 1, s.dim).astype(np.float32)).to("cuda")
+    ref32 = b.matvec(s, t, x32, torch.empty_like(x32))
+    out32 = b.matvec_noalloc(s, t, x32, torch.empty_like(x32))
+    torch.cuda.synchronize()
+    assert torch.linalg.norm(out32.double() - ref32.double()) <= 1e-5 * torch.linalg.norm(ref32.double())
+
+
+def test_noalloc_rejects_too_large_and_off_path():
+    s = b.make_sector(26, 2, 13, 2)  # D = 10,400,600 > 8,388,568 (FP64 limit)
+    t = b.make_terms(s, wl.heisenberg_terms(wl.chain_bonds(26), 1.0))
+    assert t.path == "panel"
+    lib = b.lib()
+    dummy = ctypes.c_void_p(0x1000)
+    rc = lib.dq_matvec_noalloc(s.handle, t.handle, dummy, ctypes.c_void_p(0x10000000000), b.DQ_F64, _stream())
+    assert rc == b.DQ_ERANGE
+    assert b"8388568" in lib.dq_last_error()
+    s2 = b.make_sector(12, 2, 6, 3)  # three subsystems: general path only
+    t2 = b.make_terms(s2, wl.heisenberg_terms(wl.chain_bonds(12), 1.0))
+    rc = lib.dq_matvec_noalloc(s2.handle, t2.handle, dummy, ctypes.c_void_p(0x10000000000), b.DQ_F64, _stream())
+    assert rc == b.DQ_EINVAL
