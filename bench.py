@@ -8,6 +8,7 @@ over the whole sector, x drawn from the seeded generator (U[-1,1], normalised).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload j1j2|chain|bose|xxz] [--n-sub K] [--dtype f64|f32] [--nrhs R]
+                    [--N n]   (another particle number of the same lattice, for small profiling cases)
 
 ``--impl reference`` times the CPU oracle (plain numpy, as it stands) on a bounded sample of
 rows of the same workload, on this machine's host cores; under torchrun only rank 0 runs it.
@@ -121,14 +122,27 @@ class ClockSampler:
         return {"sm_mhz": int(statistics.median(load)), "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows)}
 
 
-def build_workload(number: int, n_sub, D_only=False):
+def build_workload(number: int, n_sub, N=None):
     from paper_2407_14591_gb300 import binding as b
     from paper_2407_14591_gb300 import workloads as wl
 
     w, _ = wl.workload(number, n_sub=n_sub, draw_vector=False)
+    if N is not None:
+        w.N = N
+        w.name = f"{w.name}_as_N{N}"
     s = b.make_sector(w.L, w.Q, w.N, w.n_sub)
-    w, x = wl.workload(number, n_sub=n_sub, D=s.dim)
+    w2, x = wl.workload(number, n_sub=n_sub, D=s.dim)  # x first, then any disorder, one generator
+    w.terms = w2.terms
     return w, s, x
+
+
+def aggregate(ms_local: float, rows_local: int, steps: int, reduce_max=None, reduce_sum=None):
+    """Whole-job throughput over ranks: rows of all ranks / slowest rank's time.
+
+    reduce_max / reduce_sum reduce a float over ranks (identity on one rank)."""
+    ms = reduce_max(ms_local) if reduce_max else ms_local
+    rows = reduce_sum(float(rows_local)) if reduce_sum else float(rows_local)
+    return ms, rows * steps / (ms / 1e3)
 
 
 def oracle_rows_rate(w, partition, x, seconds: float, steps: int | None = None, warmup: int = 0):
@@ -194,6 +208,7 @@ def main():
     ap.add_argument("--n-sub", type=int, default=None)
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--N", type=int, default=None, help="override the particle number (smaller profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -217,7 +232,7 @@ def main():
     from paper_2407_14591_gb300 import binding as b
 
     number = WORKLOADS[args.workload]
-    w, s, x_np = build_workload(number, args.n_sub)
+    w, s, x_np = build_workload(number, args.n_sub, args.N)
     tdtype = torch.float64 if args.dtype == "f64" else torch.float32
     esize = 8 if args.dtype == "f64" else 4
     if args.nrhs > 1:
@@ -247,15 +262,20 @@ def main():
             b.matvec(s, t, x, y)
         ev1.record(stream)
         barrier()
-    ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        tt = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    def red(op):
+        def f(v):
+            if dist is None:
+                return v
+            tt = torch.tensor([v], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=op)
+            return float(tt.item())
+        return f
+
+    rows = s.dim * args.nrhs
+    ms, value = aggregate(ev0.elapsed_time(ev1), rows, args.steps,
+                          red(dist.ReduceOp.MAX) if dist else None, red(dist.ReduceOp.SUM) if dist else None)
     s.check_device()
     ms_step = ms / args.steps
-    rows = s.dim * args.nrhs
-    value = world * rows * args.steps / (ms / 1e3)
     alg_bytes = s.dim * args.nrhs * 2 * esize
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
