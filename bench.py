@@ -7,7 +7,7 @@ side. One step is one full product (row enumeration, diagonal, every hop, rank, 
 over the whole sector, x drawn from the seeded generator (U[-1,1], normalised).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload j1j2|chain|bose|xxz] [--n-sub K] [--dtype f64|f32] [--nrhs R]
+                    [--workload j1j2|chain|bose|xxz|batched] [--n-sub K] [--dtype f64|f32] [--nrhs R]
                     [--N n]   (another particle number of the same lattice, for small profiling cases)
 
 ``--impl reference`` times the CPU oracle (plain numpy, as it stands) on a bounded sample of
@@ -45,6 +45,7 @@ WORKLOADS = {
     "chain": 1,
     "bose": 3,
     "xxz": 5,
+    "batched": 4,
 }
 
 
@@ -198,6 +199,79 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args, world, rank, local, dist, torch):
+    """Workload 4: 64 disordered XXZ chains (L 16..26), 8 right-hand sides, one persistent launch
+    per step, tuned once, replayed from a CUDA graph."""
+    from paper_2407_14591_gb300 import binding as b
+    from paper_2407_14591_gb300 import workloads as wl
+
+    tdtype = torch.float64 if args.dtype == "f64" else torch.float32
+    esize = 8 if args.dtype == "f64" else 4
+    ws = wl.batched_chains(64, 8)
+    secs = [b.make_sector(w.L, 2, w.N, 0) for w in ws]
+    terms = [b.make_terms(s, w.terms) for s, w in zip(secs, ws)]
+    xs = [torch.from_numpy(x).to("cuda", tdtype) for x in wl.batched_vectors([s.dim for s in secs], 8)]
+    ys = [torch.empty_like(x) for x in xs]
+    batch = b.make_batch(secs, terms, 8, tdtype)
+    choice = batch.tune(xs, ys)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        batch.matvec(xs, ys)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        batch.matvec(xs, ys)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            g.replay()
+        ev1.record(stream)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+    rows = sum(s.dim for s in secs) * 8
+    ms, value = aggregate(ev0.elapsed_time(ev1), rows, args.steps)
+    ms_step = ms / args.steps
+    alg_bytes = rows * 2 * esize
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    # the same products as 64 separate launches, for comparison
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s, t, x, y in zip(secs, terms, xs, ys):
+        b.matvec(s, t, x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": "xxz_chains_64_L16to26_nrhs8", "sectors": len(secs),
+                       "D_total": sum(s.dim for s in secs), "nrhs": 8, "launch_shape": choice,
+                       "graph": True, "L2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel": "k_batch"},
+            "separate_launches_ms": seq_ms,
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -231,6 +305,12 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2407_14591_gb300 import binding as b
 
+    if args.workload == "batched":
+        run_batched(args, world, rank, local, dist, torch)
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
     number = WORKLOADS[args.workload]
     w, s, x_np = build_workload(number, args.n_sub, args.N)
     tdtype = torch.float64 if args.dtype == "f64" else torch.float32

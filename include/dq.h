@@ -168,6 +168,34 @@ int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int
  * reported by dq_check_device as DQ_EDEVICE. */
 int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* stream);
 
+/* ---- batched product ------------------------------------------------------------------- */
+
+typedef struct dq_batch dq_batch; /* opaque: up to 64 (sector, terms) pairs for one launch      */
+
+/* Plan one launch over n (1..64) Q = 2 sectors of uneven dimension (different L, N, disorder),
+ * each with nrhs (1..8) right-hand sides stored as in dq_matvec, of `dtype`. The sectors and
+ * terms must outlive the batch. Uploads the n descriptors (synchronous). FP64 vectors accumulate
+ * in FP64; FP32 vectors form products in FP32 and sum them with compensated (Neumaier)
+ * summation. Errors: DQ_EINVAL (n, nrhs, dtype out of range; terms of another sector; Q != 2),
+ * DQ_ENOMEM, DQ_ECUDA. *out is owned by the caller (dq_batch_free). */
+int dq_batch_make(int n, const dq_sector* const* sectors, const dq_terms* const* terms, int nrhs, int dtype,
+                  dq_batch** out);
+
+/* y_k = H_k x_k for every k in one persistent kernel launch (Sec. 2.2's workers over consecutive
+ * rows, here over row tiles of all sectors). x and y: host arrays of n device pointers, each to
+ * D_k * nrhs elements; x_k and y_k must not overlap. Asynchronous on `stream`; the launch
+ * contains no allocation or host synchronisation, so it can be recorded in a CUDA graph. */
+int dq_batch_matvec(dq_batch* b, const void* const* x, void* const* y, void* stream);
+
+/* Autotuner: time every launch shape (threads per CTA, CTAs per SM, rows per tile) on the given
+ * vectors (one warm-up and three timed launches each, CUDA events on `stream`), keep the
+ * fastest for later dq_batch_matvec calls and return its number in *choice (may be NULL).
+ * Overwrites y. Synchronous. */
+int dq_batch_tune(dq_batch* b, const void* const* x, void* const* y, void* stream, int* choice);
+
+/* Release a batch plan. NULL is allowed. */
+void dq_batch_free(dq_batch* b);
+
 /* Ground-state energy by Lanczos (Sec. 4.4, App. D): starting from v0 (device, D elements of
  * `dtype`, normalised inside the call, not modified), run up to `steps` steps of
  *   w = H v_k; alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1};

@@ -27,7 +27,7 @@ EXPORTED = (
     "dq_last_error", "dq_make_sector", "dq_free_sector", "dq_sector_dim", "dq_sector_partition",
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
     "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_matvec_noalloc",
-    "dq_lanczos",
+    "dq_lanczos", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free",
 )
 
 
@@ -64,6 +64,10 @@ def _load() -> ctypes.CDLL:
         "dq_terms_path": (i32, [vp, P(i32)]),
         "dq_matvec": (i32, [vp, vp, vp, vp, i32, i32, vp]),
         "dq_matvec_noalloc": (i32, [vp, vp, vp, vp, i32, vp]),
+        "dq_batch_make": (i32, [i32, P(vp), P(vp), i32, i32, P(vp)]),
+        "dq_batch_matvec": (i32, [vp, P(vp), P(vp), vp]),
+        "dq_batch_tune": (i32, [vp, P(vp), P(vp), vp, P(i32)]),
+        "dq_batch_free": (None, [vp]),
         "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
                              P(ctypes.c_double), P(i32), vp]),
     }
@@ -260,6 +264,55 @@ def matvec_noalloc(sector: Sector, terms: Terms, x, y):
     _check(_lib.dq_matvec_noalloc(sector.handle, terms.handle, ctypes.c_void_p(x.data_ptr()),
                                   ctypes.c_void_p(y.data_ptr()), _dtype_code(x), _stream_handle()))
     return y
+
+
+class Batch:
+    """One launch over many Q = 2 sectors (each with its terms), nrhs right-hand sides each."""
+
+    def __init__(self, sectors, terms, nrhs: int, dtype):
+        import torch
+
+        n = len(sectors)
+        self.sectors, self.terms, self.nrhs = list(sectors), list(terms), nrhs
+        self.dtype = dtype
+        code = DQ_F64 if dtype == torch.float64 else DQ_F32
+        sv = (ctypes.c_void_p * n)(*[s.handle.value for s in sectors])
+        tv = (ctypes.c_void_p * n)(*[t.handle.value for t in terms])
+        h = ctypes.c_void_p()
+        _check(_lib.dq_batch_make(n, sv, tv, nrhs, code, ctypes.byref(h)))
+        self._h = h
+        self.choice = None
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            _lib.dq_batch_free(h)
+            self._h = None
+
+    def _ptrs(self, xs, ys):
+        for s, x, y in zip(self.sectors, xs, ys):
+            for t, name in ((x, "x"), (y, "y")):
+                _check_vec(s, t, name)
+                if t.dtype != self.dtype or t.numel() != s.dim * self.nrhs:
+                    raise ValueError(f"{name} must hold D * nrhs elements of the batch dtype")
+        n = len(self.sectors)
+        return ((ctypes.c_void_p * n)(*[x.data_ptr() for x in xs]), (ctypes.c_void_p * n)(*[y.data_ptr() for y in ys]))
+
+    def matvec(self, xs, ys):
+        xp, yp = self._ptrs(xs, ys)
+        _check(_lib.dq_batch_matvec(self._h, xp, yp, _stream_handle()))
+        return ys
+
+    def tune(self, xs, ys) -> int:
+        xp, yp = self._ptrs(xs, ys)
+        c = ctypes.c_int()
+        _check(_lib.dq_batch_tune(self._h, xp, yp, _stream_handle(), ctypes.byref(c)))
+        self.choice = c.value
+        return c.value
+
+
+def make_batch(sectors, terms, nrhs: int, dtype) -> Batch:
+    return Batch(sectors, terms, nrhs, dtype)
 
 
 def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True) -> dict:

@@ -47,7 +47,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     """Build libdq.so if any source or header is newer than it; returns its path."""
     extra = extra or []
     srcs = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(PKG, "..", "include", "dq.h"))
     if os.path.exists(LIB) and not extra:
         t_lib = os.path.getmtime(LIB)

@@ -1,0 +1,322 @@
+// Batched product: y_k = H_k x_k for up to 64 sectors of uneven dimension (different L, N and
+// disorder), each with nrhs right-hand sides, in ONE persistent launch.
+//
+// The rows of all sectors are cut into tiles of `rows_per_tile` rows; tile t belongs to the
+// sector k with prefix[k] <= t < prefix[k+1]. Each CTA walks the tiles with a grid stride, copies
+// the descriptor of the tile's sector into shared memory when the sector changes, and runs the
+// general Q = 2 row computation (Alg. 4 unrank, bond layers, rank by Eq. (index) or Lin's two
+// tables, gather of the nrhs values of x[j], one store of y[i]). The launch shape (threads,
+// CTAs per SM, tile size) is picked by a small autotuner that times each candidate once.
+//
+// Arithmetic: FP64 vectors accumulate in FP64. FP32 vectors form products in FP32 and sum them
+// with Neumaier's compensated summation, so the error of each row sum stays at the level of one
+// FP32 rounding of its largest terms rather than growing with the number of terms.
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "dq_device.cuh"
+#include "dq_internal.h"
+
+namespace dq {
+
+constexpr int kBatchMax = 64;
+constexpr int kBatchMaxRhs = 8;
+
+struct BatchItem {
+    DevSector S;
+    DevTermsQ2 H;
+};
+
+struct BatchParams {
+    int n, nrhs, rows_per_tile;
+    unsigned long long total_tiles;
+    unsigned long long prefix[kBatchMax + 1];  // first tile of each sector
+    const BatchItem* items;
+    const void* x[kBatchMax];
+    void* y[kBatchMax];
+};
+
+template <typename T>
+struct Acc;
+template <>
+struct Acc<double> {
+    double s[kBatchMaxRhs];
+    __device__ void init(int nr, const double* d, const double* xv) {
+#pragma unroll
+        for (int c = 0; c < kBatchMaxRhs; ++c) s[c] = c < nr ? d[0] * xv[c] : 0.0;
+    }
+    __device__ void add(int nr, double a, const double* xv) {
+#pragma unroll
+        for (int c = 0; c < kBatchMaxRhs; ++c)
+            if (c < nr) s[c] += a * xv[c];
+    }
+    __device__ void store(int nr, double* yv) const {
+#pragma unroll
+        for (int c = 0; c < kBatchMaxRhs; ++c)
+            if (c < nr) yv[c] = s[c];
+    }
+};
+template <>
+struct Acc<float> {
+    float s[kBatchMaxRhs], comp[kBatchMaxRhs];
+    __device__ __forceinline__ static void two_add(float& sum, float& cp, float v) {  // Neumaier
+        float t = sum + v;
+        cp += (fabsf(sum) >= fabsf(v)) ? (sum - t) + v : (v - t) + sum;
+        sum = t;
+    }
+    __device__ void init(int nr, const double* d, const float* xv) {
+        const float df = (float)d[0];
+#pragma unroll
+        for (int c = 0; c < kBatchMaxRhs; ++c) {
+            s[c] = c < nr ? df * xv[c] : 0.f;
+            comp[c] = 0.f;
+        }
+    }
+    __device__ void add(int nr, double a, const float* xv) {
+        const float af = (float)a;
+#pragma unroll
+        for (int c = 0; c < kBatchMaxRhs; ++c)
+            if (c < nr) two_add(s[c], comp[c], af * xv[c]);
+    }
+    __device__ void store(int nr, float* yv) const {
+#pragma unroll
+        for (int c = 0; c < kBatchMaxRhs; ++c)
+            if (c < nr) yv[c] = s[c] + comp[c];
+    }
+};
+
+template <typename T>
+__device__ __forceinline__ void load_rhs(const T* p, int nr, T* v) {
+#pragma unroll
+    for (int c = 0; c < kBatchMaxRhs; ++c) v[c] = c < nr ? __ldg(p + c) : (T)0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_batch(BatchParams bp) {
+    __shared__ BatchItem it;
+    int cur = -1;  // sector whose descriptor is in `it` (same value in every thread)
+    const int nr = bp.nrhs;
+    for (unsigned long long tile = blockIdx.x; tile < bp.total_tiles; tile += gridDim.x) {
+        int k = 0;
+        while (k + 1 < bp.n && bp.prefix[k + 1] <= tile) ++k;
+        if (k != cur) {  // uniform across the CTA
+            __syncthreads();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(bp.items + k);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&it);
+            for (int q = threadIdx.x; q < (int)(sizeof(BatchItem) / 4); q += blockDim.x) dst[q] = src[q];
+            __syncthreads();
+            cur = k;
+        }
+        const DevSector& S = it.S;
+        const DevTermsQ2& H = it.H;
+        const T* x = reinterpret_cast<const T*>(bp.x[k]);
+        T* y = reinterpret_cast<T*>(bp.y[k]);
+        const unsigned long long r0 = (tile - bp.prefix[k]) * (unsigned long long)bp.rows_per_tile;
+        const unsigned long long r1 = min(r0 + (unsigned long long)bp.rows_per_tile, (unsigned long long)S.D);
+        const bool lin2 = S.n_sub == 2;
+        for (unsigned long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+            const uint64_t s = d_unrank(S, S.off, S.str, i);
+            double d = H.C;
+            if (H.lin) {
+                uint64_t m = s;
+                while (m) {
+                    int p = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    d += __ldg(H.lin + p);
+                }
+            }
+            for (int l = 0; l < H.nl; ++l) {
+                uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+                if (H.kpos[l] < 0) {
+                    d += H.K[l] * (double)__popcll(a);
+                } else {
+                    while (a) {
+                        int p = __ffsll((long long)a) - 1;
+                        a &= a - 1;
+                        d += __ldg(H.pos + H.kpos[l] + p);
+                    }
+                }
+            }
+            T xv[kBatchMaxRhs];
+            load_rhs(x + i * nr, nr, xv);
+            Acc<T> acc;
+            acc.init(nr, &d, xv);
+            for (int l = 0; l < H.nl; ++l) {
+                uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
+                const uint64_t pm = 1ull | (1ull << H.dist[l]);
+                while (o) {
+                    int p = __ffsll((long long)o) - 1;
+                    o &= o - 1;
+                    const uint64_t s2 = s ^ (pm << p);
+                    const uint64_t j = lin2 ? d_rank_lin2(S, s2) : d_rank(S, S.off, S.str, s2);
+                    const double amp = H.apos[l] < 0 ? H.A[l] : __ldg(H.pos + H.apos[l] + p);
+                    load_rhs(x + j * nr, nr, xv);
+                    acc.add(nr, amp, xv);
+                }
+            }
+            acc.store(nr, y + i * nr);
+        }
+    }
+}
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms > 0 ? sms : 1;
+}
+
+// Launch-shape candidates of the autotuner: (threads, CTAs per SM, rows per tile).
+struct Shape {
+    int threads, per_sm, tile;
+};
+static const Shape kShapes[] = {{128, 8, 2048}, {256, 4, 4096}, {256, 8, 2048}, {512, 2, 8192}, {512, 4, 4096},
+                                {256, 4, 16384}};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+}  // namespace dq
+
+struct dq_batch {
+    int n, nrhs, dtype, shape;
+    std::vector<unsigned long long> dims;
+    void* items;  // device array of BatchItem
+    int device;
+};
+
+using namespace dq;
+
+static int batch_launch(dq_batch* b, const void* const* x, void* const* y, cudaStream_t st, int shape) {
+    const Shape& sh = kShapes[shape];
+    BatchParams bp;
+    std::memset(&bp, 0, sizeof bp);
+    bp.n = b->n;
+    bp.nrhs = b->nrhs;
+    bp.rows_per_tile = sh.tile;
+    bp.items = reinterpret_cast<const BatchItem*>(b->items);
+    unsigned long long t = 0;
+    for (int k = 0; k < b->n; ++k) {
+        bp.prefix[k] = t;
+        t += (b->dims[k] + sh.tile - 1) / sh.tile;
+        bp.x[k] = x[k];
+        bp.y[k] = y[k];
+    }
+    bp.prefix[b->n] = t;
+    bp.total_tiles = t;
+    unsigned long long cap = (unsigned long long)sm_count() * sh.per_sm;
+    unsigned grid = (unsigned)(t < cap ? (t ? t : 1) : cap);
+    if (b->dtype == DQ_F64)
+        k_batch<double><<<grid, sh.threads, 0, st>>>(bp);
+    else
+        k_batch<float><<<grid, sh.threads, 0, st>>>(bp);
+    return (int)cudaGetLastError();
+}
+
+extern "C" {
+
+int dq_batch_make(int n, const dq_sector* const* sectors, const dq_terms* const* terms, int nrhs, int dtype,
+                  dq_batch** out) {
+    clear_error();
+    if (!out || !sectors || !terms) return set_error(DQ_EINVAL, "NULL argument");
+    *out = nullptr;
+    if (n < 1 || n > kBatchMax) return set_error(DQ_EINVAL, "n must be in [1, %d]", kBatchMax);
+    if (nrhs < 1 || nrhs > kBatchMaxRhs) return set_error(DQ_EINVAL, "nrhs must be in [1, %d]", kBatchMaxRhs);
+    if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
+    std::vector<BatchItem> host(n);
+    dq_batch* b = new (std::nothrow) dq_batch();
+    if (!b) return set_error(DQ_ENOMEM, "host allocation");
+    b->n = n;
+    b->nrhs = nrhs;
+    b->dtype = dtype;
+    b->shape = 1;
+    b->items = nullptr;
+    for (int k = 0; k < n; ++k) {
+        const dq_sector* s = sectors[k];
+        const dq_terms* t = terms[k];
+        if (!s || !t || t->sector != s) {
+            delete b;
+            return set_error(DQ_EINVAL, "item %d: NULL or terms of another sector", k);
+        }
+        if (!s->has_device) {
+            delete b;
+            return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
+        }
+        if (!t->q2) {
+            delete b;
+            return set_error(DQ_EINVAL, "item %d: the batched product serves Q = 2 sectors", k);
+        }
+        host[k].S = s->dev;
+        host[k].H = t->q2v;
+        b->dims.push_back(s->D);
+    }
+    cudaError_t e = cudaMalloc(&b->items, sizeof(BatchItem) * n);
+    if (e != cudaSuccess) {
+        delete b;
+        return set_error(DQ_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(b->items, host.data(), sizeof(BatchItem) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(b->items);
+        delete b;
+        return set_error(DQ_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    }
+    cudaGetDevice(&b->device);
+    *out = b;
+    return DQ_OK;
+}
+
+void dq_batch_free(dq_batch* b) {
+    if (!b) return;
+    cudaFree(b->items);
+    delete b;
+}
+
+int dq_batch_matvec(dq_batch* b, const void* const* x, void* const* y, void* stream) {
+    clear_error();
+    if (!b || !x || !y) return set_error(DQ_EINVAL, "NULL argument");
+    for (int k = 0; k < b->n; ++k)
+        if (!x[k] || !y[k]) return set_error(DQ_EINVAL, "item %d: NULL vector", k);
+    int e = batch_launch(b, x, y, (cudaStream_t)stream, b->shape);
+    if (e) return set_error(DQ_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)e));
+    return DQ_OK;
+}
+
+int dq_batch_tune(dq_batch* b, const void* const* x, void* const* y, void* stream, int* choice) {
+    clear_error();
+    if (!b || !x || !y) return set_error(DQ_EINVAL, "NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_i = b->shape;
+    for (int i = 0; i < kNumShapes; ++i) {
+        int rc = batch_launch(b, x, y, st, i);  // warm-up
+        if (rc) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return set_error(DQ_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)rc));
+        }
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) batch_launch(b, x, y, st, i);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_i = i;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->shape = best_i;
+    if (choice) *choice = best_i;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(DQ_ECUDA, "batch tune: %s", cudaGetErrorString(e));
+    return DQ_OK;
+}
+
+}  // extern "C"

@@ -13,104 +13,10 @@
 
 #include <cuda_runtime.h>
 
+#include "dq_device.cuh"
 #include "dq_internal.h"
 
 namespace dq {
-
-__device__ __forceinline__ int digit_sum(uint32_t f, int nb) {
-    switch (nb) {
-        case 1: return __popc(f);
-        case 2: return __popc(f & 0x55555555u) + 2 * __popc(f & 0xAAAAAAAAu);
-        case 3: return __popc(f & 0x49249249u) + 2 * __popc(f & 0x92492492u) + 4 * __popc(f & 0x24924924u);
-        default:
-            return __popc(f & 0x11111111u) + 2 * __popc(f & 0x22222222u) + 4 * __popc(f & 0x44444444u) +
-                   8 * __popc(f & 0x88888888u);
-    }
-}
-
-__device__ __forceinline__ uint32_t field_of(const DevSector& S, uint64_t w, int k) {
-    return (uint32_t)((w >> S.shift[k]) & ((1ull << (S.nb * S.Lk[k])) - 1));
-}
-
-// Eq. (index) for a valid state. off_s / str_s may live in shared or global memory.
-__device__ __forceinline__ uint64_t d_rank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t w) {
-    uint64_t idx = 0;
-    int lam = 0;
-    for (int k = 0; k < S.n_sub; ++k) {
-        uint32_t f = field_of(S, w, k);
-        uint32_t li = __ldg(S.rank_tab[S.tab[k]] + f);
-        int n = digit_sum(f, S.nb);
-        int o = S.os_base[k] + lam * S.os_ld[k] + n;
-        idx += off_s[o] + str_s[o] * (uint64_t)li;
-        lam += n;
-    }
-    return idx;
-}
-
-// Lin's two-table form (Sec. 3.3): index = c_0(sigma^(0)) + index_1(sigma^(1)).
-__device__ __forceinline__ uint64_t d_rank_lin2(const DevSector& S, uint64_t w) {
-    uint32_t f0 = (uint32_t)(w >> S.shift[0]);
-    uint32_t f1 = (uint32_t)(w & ((1ull << (S.nb * S.Lk[1])) - 1));
-    return __ldg(S.c0_tab + f0) + (uint64_t)__ldg(S.rank_tab[S.tab[1]] + f1);
-}
-
-// Alg. 4 for idx < D.
-__device__ __forceinline__ uint64_t d_unrank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t idx) {
-    uint64_t w = 0;
-    int lam = 0;
-    for (int k = 0; k < S.n_sub; ++k) {
-        int base = S.os_base[k] + lam * S.os_ld[k];
-        int n;
-        uint64_t li;
-        if (k == S.n_sub - 1) {
-            n = S.N - lam;
-            li = idx;  // offset 0, stride 1 for the last subsystem
-            idx = 0;
-        } else {
-            n = 0;
-            while (n < S.nmax[k] && !(idx < off_s[base + n + 1])) ++n;
-            idx -= off_s[base + n];
-            uint64_t st = str_s[base + n];
-            li = idx / st;
-            idx -= li * st;
-        }
-        int t = S.tab[k];
-        uint32_t pat = __ldg(S.unrank_tab[t] + __ldg(S.sec_start[t] + n) + li);
-        w |= (uint64_t)pat << S.shift[k];
-        lam += n;
-    }
-    return w;
-}
-
-__device__ __forceinline__ bool d_valid(const DevSector& S, uint64_t w) {
-    int bits = S.L * S.nb;
-    if (bits < 64 && (w >> bits) != 0) return false;
-    int n = 0;
-    unsigned m = (1u << S.nb) - 1;
-    for (int i = 0; i < S.L; ++i) {
-        int d = (int)((w >> (S.nb * i)) & m);
-        if (d >= S.Q) return false;
-        n += d;
-    }
-    return n == S.N;
-}
-
-// Stage the offset / stride tables in shared memory when they fit.
-__device__ __forceinline__ void stage_os(const DevSector& S, uint64_t* sm, bool use, const uint64_t*& off_s,
-                                         const uint64_t*& str_s) {
-    if (use) {
-        for (int q = threadIdx.x; q < S.os_total; q += blockDim.x) {
-            sm[q] = S.off[q];
-            sm[S.os_total + q] = S.str[q];
-        }
-        __syncthreads();
-        off_s = sm;
-        str_s = sm + S.os_total;
-    } else {
-        off_s = S.off;
-        str_s = S.str;
-    }
-}
 
 __global__ void k_state_at(DevSector S, const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n,
                            bool use_sm) {
