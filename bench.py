@@ -7,7 +7,7 @@ side. One step is one full product (row enumeration, diagonal, every hop, rank, 
 over the whole sector, x drawn from the seeded generator (U[-1,1], normalised).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload j1j2|chain|bose|xxz|batched] [--n-sub K] [--dtype f64|f32] [--nrhs R]
+                    [--workload j1j2|chain|bose|xxz|batched|diff] [--n-sub K] [--dtype f64|f32] [--nrhs R]
                     [--N n]   (another particle number of the same lattice, for small profiling cases)
 
 ``--impl reference`` times the CPU oracle (plain numpy, as it stands) on a bounded sample of
@@ -46,6 +46,7 @@ WORKLOADS = {
     "bose": 3,
     "xxz": 5,
     "batched": 4,
+    "diff": 5,
 }
 
 
@@ -272,6 +273,69 @@ def run_batched(args, world, rank, local, dist, torch):
         print(json.dumps(line), flush=True)
 
 
+def run_diff(args, world, rank, local, dist, torch):
+    """Workload 5 as a training step: y = H(theta) x forward and the hand-written adjoint
+    (dx = H dy, dtheta_k = <dy, T_k x>) backward, theta = 24 couplings + 24 fields."""
+    from paper_2407_14591_gb300 import autograd as ag
+    from paper_2407_14591_gb300 import binding as b
+    from paper_2407_14591_gb300 import workloads as wl
+
+    tdtype = torch.float64 if args.dtype == "f64" else torch.float32
+    esize = 8 if args.dtype == "f64" else 4
+    s = b.make_sector(24, 2, 12, 2)
+    w, x_np = wl.workload(5, D=s.dim)
+    params = []
+    for bnd, (i, j) in enumerate(wl.chain_bonds(24)):
+        params.append(("XY", i, j, bnd, 1.0))
+        params.append(("ZZ", i, j, bnd, 1.0))
+    for i in range(24):
+        params.append(("Z", i, -1, 24 + i, 1.0))
+    op = ag.ParamOperator(s, params, n_params=48)
+    theta = torch.tensor([t[3] for t in w.terms if t[0] == "XY"] + [t[3] for t in w.terms if t[0] == "Z"],
+                         dtype=torch.float64, requires_grad=True)
+    x = torch.from_numpy(x_np).to("cuda", tdtype).requires_grad_(True)
+    r = torch.ones_like(x)
+
+    def step():
+        theta.grad = None
+        x.grad = None
+        y = ag.matvec(op, x, theta)
+        y.backward(r)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms, value = aggregate(ev0.elapsed_time(ev1), s.dim, args.steps)
+    ms_step = ms / args.steps
+    # forward product, backward product, per-term reduction: x, y, dy, dx and x again
+    alg_bytes = s.dim * esize * 6
+    peak, peak_kind = hbm_peak()
+    achieved = alg_bytes / (ms_step / 1e3) / 1e9
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": "disordered_xxz_L24_N12_forward_backward", "D": s.dim, "params": 48,
+                       "step": "y = H(theta) x, then dx and dtheta"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
+                         "kernel": "k_matvec_q2 + k_term_grads"},
+            "clocks": clk.summary(),
+            "gpu_launches": args.steps * 6,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -305,8 +369,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2407_14591_gb300 import binding as b
 
-    if args.workload == "batched":
-        run_batched(args, world, rank, local, dist, torch)
+    if args.workload in ("batched", "diff"):
+        (run_batched if args.workload == "batched" else run_diff)(args, world, rank, local, dist, torch)
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()

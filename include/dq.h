@@ -168,6 +168,21 @@ int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int
  * reported by dq_check_device as DQ_EDEVICE. */
 int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* stream);
 
+/* ---- differentiation ---------------------------------------------------------------------- */
+
+/* Coefficient gradients of the product (the adjoint of y = H x with H = sum_q coef_q T_q): for
+ * the given list of terms (only kind, i, j are used; coef is ignored) and a cotangent dy,
+ *   d_grads[q] = sum_i sum_r dy[i, r] (T_q x)[i, r],
+ * T_q being term q with coefficient 1 (the operators of DQ_XY .. DQ_U). With a complex vector
+ * stored as nrhs = 2 real columns this is Re <dy, T_q x>. The gradient with respect to x is
+ * H dy (every term is real and Hermitian), i.e. another dq_matvec. x, dy: device arrays laid out
+ * as in dq_matvec; d_grads: device array of n_terms doubles. Accumulation in FP64, reduced in a
+ * fixed order (deterministic). Allocates and frees a small workspace; synchronous.
+ * Errors as dq_make_terms, plus DQ_EINVAL for bad dtype or nrhs. The paper's operator class
+ * (Sec. 4.1) has no derivatives; this serves training-style use of the product. */
+int dq_term_grads(const dq_sector* s, const dq_term* terms, int n_terms, const void* x, const void* dy, int dtype,
+                  int nrhs, double* d_grads, void* stream);
+
 /* ---- batched product ------------------------------------------------------------------- */
 
 typedef struct dq_batch dq_batch; /* opaque: up to 64 (sector, terms) pairs for one launch      */

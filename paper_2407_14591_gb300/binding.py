@@ -27,7 +27,7 @@ EXPORTED = (
     "dq_last_error", "dq_make_sector", "dq_free_sector", "dq_sector_dim", "dq_sector_partition",
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
     "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_matvec_noalloc",
-    "dq_lanczos", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free",
+    "dq_lanczos", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free", "dq_term_grads",
 )
 
 
@@ -68,6 +68,7 @@ def _load() -> ctypes.CDLL:
         "dq_batch_matvec": (i32, [vp, P(vp), P(vp), vp]),
         "dq_batch_tune": (i32, [vp, P(vp), P(vp), vp, P(i32)]),
         "dq_batch_free": (None, [vp]),
+        "dq_term_grads": (i32, [vp, P(_Term), i32, vp, vp, i32, i32, vp, vp]),
         "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
                              P(ctypes.c_double), P(i32), vp]),
     }
@@ -309,6 +310,27 @@ class Batch:
         _check(_lib.dq_batch_tune(self._h, xp, yp, _stream_handle(), ctypes.byref(c)))
         self.choice = c.value
         return c.value
+
+
+def term_grads(sector: Sector, terms, x, dy):
+    """g_q = sum_i sum_r dy[i, r] (T_q x)[i, r] for each (kind, i, j[, coef]) in ``terms``;
+    returns a float64 CUDA tensor of len(terms)."""
+    import torch
+
+    _check_vec(sector, x, "x")
+    _check_vec(sector, dy, "dy")
+    if dy.dtype != x.dtype or dy.shape != x.shape:
+        raise ValueError("x and dy must have the same dtype and shape")
+    arr = (_Term * max(1, len(terms)))()
+    for q, t in enumerate(terms):
+        kind, i, j = t[0], t[1], t[2]
+        arr[q] = _Term(KINDS[kind] if isinstance(kind, str) else int(kind), int(i), int(j), 0.0)
+    out = torch.empty(max(1, len(terms)), dtype=torch.float64, device=x.device)
+    nrhs = 1 if x.dim() == 1 else x.shape[1]
+    _check(_lib.dq_term_grads(sector.handle, arr, len(terms), ctypes.c_void_p(x.data_ptr()),
+                              ctypes.c_void_p(dy.data_ptr()), _dtype_code(x), nrhs, ctypes.c_void_p(out.data_ptr()),
+                              _stream_handle()))
+    return out[: len(terms)]
 
 
 def make_batch(sectors, terms, nrhs: int, dtype) -> Batch:
