@@ -7,7 +7,7 @@ side. One step is one full product (row enumeration, diagonal, every hop, rank, 
 over the whole sector, x drawn from the seeded generator (U[-1,1], normalised).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload j1j2|chain|bose|xxz|batched|diff] [--n-sub K] [--dtype f64|f32] [--nrhs R]
+                    [--workload j1j2|chain|bose|xxz|batched|diff|rank] [--n-sub K] [--dtype f64|f32] [--nrhs R]
                     [--N n]   (another particle number of the same lattice, for small profiling cases)
 
 ``--impl reference`` times the CPU oracle (plain numpy, as it stands) on a bounded sample of
@@ -47,6 +47,7 @@ WORKLOADS = {
     "xxz": 5,
     "batched": 4,
     "diff": 5,
+    "rank": 0,
 }
 
 
@@ -336,6 +337,49 @@ def run_diff(args, world, rank, local, dist, torch):
         print(json.dumps(line), flush=True)
 
 
+RANK_SWEEP = [  # (L, Q, N, n_sub): Fig. 4-6 analogue; half filling unless stated
+    (20, 2, 10, 1), (20, 2, 10, 2), (20, 2, 10, 4), (20, 2, 10, 20),
+    (24, 2, 12, 1), (24, 2, 12, 2), (24, 2, 12, 3), (24, 2, 12, 6), (24, 2, 12, 24),
+    (28, 2, 14, 2), (28, 2, 14, 3), (28, 2, 14, 4), (28, 2, 14, 7),
+    (32, 2, 16, 2), (32, 2, 16, 3), (32, 2, 16, 4), (32, 2, 16, 8), (32, 2, 16, 32),
+    (32, 2, 4, 2), (32, 2, 4, 4),
+    (12, 4, 18, 1), (12, 4, 18, 2), (12, 4, 18, 3), (16, 4, 24, 2), (16, 4, 24, 4),
+]
+
+
+def run_rank(args, world, rank, local, dist, torch):
+    """Function (i) throughput: index_of_batch on 2^24 random valid states per configuration
+    (states from state_at_batch on random indices), one JSON line per configuration."""
+    from paper_2407_14591_gb300 import binding as b
+
+    n = 1 << 24
+    g = torch.Generator(device="cpu").manual_seed(20240719)
+    for (L, Q, N, n_sub) in RANK_SWEEP:
+        s = b.make_sector(L, Q, N, n_sub)
+        idx = (torch.rand(n, generator=g, dtype=torch.float64) * s.dim).long().clamp_(max=s.dim - 1).to("cuda")
+        st = s.state_at_batch(idx)
+        out = torch.empty_like(idx)
+        for _ in range(max(1, args.warmup)):
+            s.index_of_batch(st, out)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(args.steps):
+            s.index_of_batch(st, out)
+        ev1.record()
+        torch.cuda.synchronize()
+        s.check_device()
+        ok = bool(torch.equal(out, idx))
+        ms = ev0.elapsed_time(ev1) / args.steps
+        nb = (Q - 1).bit_length()
+        table_bytes = sum(4 << (nb * Lk) for Lk in set(s.partition))
+        if rank == 0:
+            print(json.dumps({"metric": "ranks/s", "value": n / (ms / 1e3), "unit": "ranks/s", "L": L, "Q": Q,
+                              "N": N, "n_sub": s.n_sub, "partition": s.partition, "D": s.dim,
+                              "rank_table_bytes": table_bytes, "ms": ms, "states": n, "roundtrip_ok": ok}),
+                  flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -369,8 +413,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2407_14591_gb300 import binding as b
 
-    if args.workload in ("batched", "diff"):
-        (run_batched if args.workload == "batched" else run_diff)(args, world, rank, local, dist, torch)
+    if args.workload in ("batched", "diff", "rank"):
+        {"batched": run_batched, "diff": run_diff, "rank": run_rank}[args.workload](args, world, rank, local, dist,
+                                                                                    torch)
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()

@@ -8,9 +8,9 @@
 // tables, gather of the nrhs values of x[j], one store of y[i]). The launch shape (threads,
 // CTAs per SM, tile size) is picked by a small autotuner that times each candidate once.
 //
-// Arithmetic: FP64 vectors accumulate in FP64. FP32 vectors form products in FP32 and sum them
-// with Neumaier's compensated summation, so the error of each row sum stays at the level of one
-// FP32 rounding of its largest terms rather than growing with the number of terms.
+// Arithmetic: FP64 vectors accumulate in FP64. FP32 vectors use the FP32 copies of the
+// coefficients, form products in FP32 and sum them with Neumaier's compensated summation, so the
+// error of each row sum stays at about one FP32 rounding instead of growing with its length.
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -39,54 +39,14 @@ struct BatchParams {
     void* y[kBatchMax];
 };
 
+// Coefficient in the vectors' precision (FP64 vectors: the FP64 value; FP32: its FP32 copy).
 template <typename T>
-struct Acc;
-template <>
-struct Acc<double> {
-    double s[kBatchMaxRhs];
-    __device__ void init(int nr, const double* d, const double* xv) {
-#pragma unroll
-        for (int c = 0; c < kBatchMaxRhs; ++c) s[c] = c < nr ? d[0] * xv[c] : 0.0;
-    }
-    __device__ void add(int nr, double a, const double* xv) {
-#pragma unroll
-        for (int c = 0; c < kBatchMaxRhs; ++c)
-            if (c < nr) s[c] += a * xv[c];
-    }
-    __device__ void store(int nr, double* yv) const {
-#pragma unroll
-        for (int c = 0; c < kBatchMaxRhs; ++c)
-            if (c < nr) yv[c] = s[c];
-    }
-};
-template <>
-struct Acc<float> {
-    float s[kBatchMaxRhs], comp[kBatchMaxRhs];
-    __device__ __forceinline__ static void two_add(float& sum, float& cp, float v) {  // Neumaier
-        float t = sum + v;
-        cp += (fabsf(sum) >= fabsf(v)) ? (sum - t) + v : (v - t) + sum;
-        sum = t;
-    }
-    __device__ void init(int nr, const double* d, const float* xv) {
-        const float df = (float)d[0];
-#pragma unroll
-        for (int c = 0; c < kBatchMaxRhs; ++c) {
-            s[c] = c < nr ? df * xv[c] : 0.f;
-            comp[c] = 0.f;
-        }
-    }
-    __device__ void add(int nr, double a, const float* xv) {
-        const float af = (float)a;
-#pragma unroll
-        for (int c = 0; c < kBatchMaxRhs; ++c)
-            if (c < nr) two_add(s[c], comp[c], af * xv[c]);
-    }
-    __device__ void store(int nr, float* yv) const {
-#pragma unroll
-        for (int c = 0; c < kBatchMaxRhs; ++c)
-            if (c < nr) yv[c] = s[c] + comp[c];
-    }
-};
+__device__ __forceinline__ T bcf(double d, float f) {
+    if constexpr (sizeof(T) == 8)
+        return d;
+    else
+        return f;
+}
 
 template <typename T>
 __device__ __forceinline__ void load_rhs(const T* p, int nr, T* v) {
@@ -117,47 +77,83 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams bp) {
         const unsigned long long r0 = (tile - bp.prefix[k]) * (unsigned long long)bp.rows_per_tile;
         const unsigned long long r1 = min(r0 + (unsigned long long)bp.rows_per_tile, (unsigned long long)S.D);
         const bool lin2 = S.n_sub == 2;
+        const T* posT = sizeof(T) == 8 ? (const T*)H.pos : (const T*)H.posf;
         for (unsigned long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
             const uint64_t s = d_unrank(S, S.off, S.str, i);
-            double d = H.C;
-            if (H.lin) {
-                uint64_t m = s;
-                while (m) {
-                    int p = __ffsll((long long)m) - 1;
-                    m &= m - 1;
-                    d += __ldg(H.lin + p);
-                }
-            }
-            for (int l = 0; l < H.nl; ++l) {
-                uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
-                if (H.kpos[l] < 0) {
-                    d += H.K[l] * (double)__popcll(a);
-                } else {
-                    while (a) {
-                        int p = __ffsll((long long)a) - 1;
-                        a &= a - 1;
-                        d += __ldg(H.pos + H.kpos[l] + p);
+            // diagonal: FP64 vectors in FP64; FP32 vectors with FP32 coefficients, compensated
+            T dv;
+            if constexpr (sizeof(T) == 8) {
+                double d = H.C;
+                if (H.lin) {
+                    uint64_t m = s;
+                    while (m) {
+                        int p = __ffsll((long long)m) - 1;
+                        m &= m - 1;
+                        d += __ldg(H.lin + p);
                     }
                 }
+                for (int l = 0; l < H.nl; ++l) {
+                    uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+                    if (H.kpos[l] < 0) {
+                        d += __ldg(H.KA + l) * (double)__popcll(a);
+                    } else {
+                        while (a) {
+                            int p = __ffsll((long long)a) - 1;
+                            a &= a - 1;
+                            d += __ldg(H.pos + H.kpos[l] + p);
+                        }
+                    }
+                }
+                dv = d;
+            } else {
+                RowAcc<float> d;
+                d.init(H.Cf);
+                if (H.linf) {
+                    uint64_t m = s;
+                    while (m) {
+                        int p = __ffsll((long long)m) - 1;
+                        m &= m - 1;
+                        d.add(__ldg(H.linf + p));
+                    }
+                }
+                for (int l = 0; l < H.nl; ++l) {
+                    uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+                    if (H.kpos[l] < 0) {
+                        if (a) d.add(__ldg(H.KAf + l) * (float)__popcll(a));
+                    } else {
+                        while (a) {
+                            int p = __ffsll((long long)a) - 1;
+                            a &= a - 1;
+                            d.add(__ldg(H.posf + H.kpos[l] + p));
+                        }
+                    }
+                }
+                dv = d.get();
             }
             T xv[kBatchMaxRhs];
             load_rhs(x + i * nr, nr, xv);
-            Acc<T> acc;
-            acc.init(nr, &d, xv);
+            RowAcc<T> acc[kBatchMaxRhs];
+#pragma unroll
+            for (int c = 0; c < kBatchMaxRhs; ++c) acc[c].init(c < nr ? dv * xv[c] : (T)0);
             for (int l = 0; l < H.nl; ++l) {
                 uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
                 const uint64_t pm = 1ull | (1ull << H.dist[l]);
+                const T au = bcf<T>(__ldg(H.KA + kMaxLayers + l), __ldg(H.KAf + kMaxLayers + l));
                 while (o) {
                     int p = __ffsll((long long)o) - 1;
                     o &= o - 1;
                     const uint64_t s2 = s ^ (pm << p);
                     const uint64_t j = lin2 ? d_rank_lin2(S, s2) : d_rank(S, S.off, S.str, s2);
-                    const double amp = H.apos[l] < 0 ? H.A[l] : __ldg(H.pos + H.apos[l] + p);
+                    const T amp = H.apos[l] < 0 ? au : __ldg(posT + H.apos[l] + p);
                     load_rhs(x + j * nr, nr, xv);
-                    acc.add(nr, amp, xv);
+#pragma unroll
+                    for (int c = 0; c < kBatchMaxRhs; ++c)
+                        if (c < nr) acc[c].add(amp * xv[c]);
                 }
             }
-            acc.store(nr, y + i * nr);
+#pragma unroll
+            for (int c = 0; c < kBatchMaxRhs; ++c)
+                if (c < nr) y[i * nr + c] = acc[c].get();
         }
     }
 }

@@ -75,6 +75,16 @@ __device__ __forceinline__ uint64_t d_unrank(const DevSector& S, const uint64_t*
 __device__ __forceinline__ bool d_valid(const DevSector& S, uint64_t w) {
     int bits = S.L * S.nb;
     if (bits < 64 && (w >> bits) != 0) return false;
+    if ((S.Q & (S.Q - 1)) == 0) {
+        // Q = 2^Nbits: every digit is < Q; the digit sum is a weighted popcount of bit planes
+        int n = 0;
+        for (int b = 0; b < S.nb; ++b) {
+            uint64_t plane = 0;
+            for (int q = b; q < 64; q += S.nb) plane |= 1ull << q;
+            n += __popcll(w & plane) << b;
+        }
+        return n == S.N;
+    }
     int n = 0;
     unsigned m = (1u << S.nb) - 1;
     for (int i = 0; i < S.L; ++i) {
@@ -102,5 +112,32 @@ __device__ __forceinline__ void stage_os(const DevSector& S, uint64_t* sm, bool 
     }
 }
 
+
+// Row accumulator: plain FP64 for FP64 vectors; for FP32 vectors FP32 products summed with
+// Neumaier's compensated summation (the running error term keeps each row sum within about one
+// FP32 rounding of its exact value, however many terms it has).
+template <typename T>
+struct RowAcc;
+template <>
+struct RowAcc<double> {
+    double s;
+    __device__ __forceinline__ void init(double v) { s = v; }
+    __device__ __forceinline__ void add(double v) { s += v; }
+    __device__ __forceinline__ double get() const { return s; }
+};
+template <>
+struct RowAcc<float> {
+    float s, c;
+    __device__ __forceinline__ void init(float v) {
+        s = v;
+        c = 0.f;
+    }
+    __device__ __forceinline__ void add(float v) {
+        const float t = s + v;
+        c += (fabsf(s) >= fabsf(v)) ? (s - t) + v : (v - t) + s;
+        s = t;
+    }
+    __device__ __forceinline__ float get() const { return s + c; }
+};
 
 }  // namespace dq

@@ -46,12 +46,20 @@ struct DevTermsQ2 {
     int dist[kMaxLayers];
     uint64_t dmask[kMaxLayers];  // low positions p with a diagonal coefficient
     uint64_t omask[kMaxLayers];  // low positions p with an off-diagonal amplitude
-    double K[kMaxLayers];        // uniform coefficient of [sigma_p != sigma_{p+dist}]
-    double A[kMaxLayers];        // uniform hop amplitude
+    const double* KA;            // [2 * kMaxLayers] device array: uniform coefficient K of
+                                 // [sigma_p != sigma_{p+dist}] at l, uniform hop amplitude A at
+                                 // kMaxLayers + l
     int kpos[kMaxLayers];        // -1: uniform K; else offset of 64 per-position values in pos
     int apos[kMaxLayers];        // -1: uniform A; else offset in pos
     const double* pos;           // per-position coefficients
+    // FP32 copies of the coefficients, used when the vectors are FP32 (device arrays, so that
+    // the structure stays small enough to be passed by value: kernel parameters <= 4 KB)
+    float Cf;
+    const float* KAf;  // [2 * kMaxLayers]: K of layer l at l, A of layer l at kMaxLayers + l
+    const float* linf;
+    const float* posf;
 };
+static_assert(sizeof(DevSector) + sizeof(DevTermsQ2) + 64 <= 4096, "product kernel parameters exceed 4 KB");
 
 // General-Q operator (bosons): per-site digit functions, density-density pairs, hops.
 struct DevTermsQG {
@@ -66,6 +74,12 @@ struct DevTermsQG {
     const int* hop_sh;     // [nhop][2] shifts (a, b): term -t (b+_a b_b + b+_b b_a)
     const double* hop_t;
     const double* amp;     // [Q][Q]: sqrt((n_a + 1) n_b)
+    // FP32 copies of the coefficients, used when the vectors are FP32
+    float Cf;
+    const float* site_ff;
+    const float* pair_Kf;
+    const float* hop_tf;
+    const float* ampf;
 };
 
 // Plan of the panel product (Q = 2, two subsystems, Sec. 3.3): with index = c_0(s0) + index_1(s1),

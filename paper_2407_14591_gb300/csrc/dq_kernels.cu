@@ -52,9 +52,13 @@ __global__ void k_index_of(DevSector S, const uint64_t* __restrict__ in, uint64_
 
 constexpr int kMaxCh = 8;  // right-hand sides handled per pass
 
+// Coefficient in the vectors' precision (FP64 vectors: the FP64 value; FP32: its FP32 copy).
 template <typename T>
-__device__ __forceinline__ double ld_as_double(const T* p) {
-    return (double)__ldg(p);
+__device__ __forceinline__ T cf(double d, float f) {
+    if constexpr (sizeof(T) == 8)
+        return d;
+    else
+        return f;
 }
 
 // y = H x, Q = 2 operator in bond-layer form. LIN2 selects the two-table rank.
@@ -64,52 +68,83 @@ __global__ void __launch_bounds__(256) k_matvec_q2(DevSector S, DevTermsQ2 H, co
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
+    const T* posT = sizeof(T) == 8 ? (const T*)H.pos : (const T*)H.posf;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = d_unrank(S, off_s, str_s, i);
-        double d = H.C;
-        if (H.lin) {
-            uint64_t m = s;
-            while (m) {
-                int p = __ffsll((long long)m) - 1;
-                m &= m - 1;
-                d += H.lin[p];
-            }
-        }
-        for (int l = 0; l < H.nl; ++l) {
-            uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
-            if (H.kpos[l] < 0) {
-                d += H.K[l] * (double)__popcll(a);
-            } else {
-                while (a) {
-                    int p = __ffsll((long long)a) - 1;
-                    a &= a - 1;
-                    d += H.pos[H.kpos[l] + p];
+        // diagonal: FP64 vectors in FP64; FP32 vectors with FP32 coefficients, compensated
+        T dv;
+        if constexpr (sizeof(T) == 8) {
+            double d = H.C;
+            if (H.lin) {
+                uint64_t m = s;
+                while (m) {
+                    int p = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    d += H.lin[p];
                 }
             }
+            for (int l = 0; l < H.nl; ++l) {
+                uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+                if (H.kpos[l] < 0) {
+                    d += __ldg(H.KA + l) * (double)__popcll(a);
+                } else {
+                    while (a) {
+                        int p = __ffsll((long long)a) - 1;
+                        a &= a - 1;
+                        d += H.pos[H.kpos[l] + p];
+                    }
+                }
+            }
+            dv = d;
+        } else {
+            RowAcc<float> d;
+            d.init(H.Cf);
+            if (H.linf) {
+                uint64_t m = s;
+                while (m) {
+                    int p = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    d.add(H.linf[p]);
+                }
+            }
+            for (int l = 0; l < H.nl; ++l) {
+                uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+                if (H.kpos[l] < 0) {
+                    if (a) d.add(__ldg(H.KAf + l) * (float)__popcll(a));
+                } else {
+                    while (a) {
+                        int p = __ffsll((long long)a) - 1;
+                        a &= a - 1;
+                        d.add(H.posf[H.kpos[l] + p]);
+                    }
+                }
+            }
+            dv = d.get();
         }
-        double acc[kMaxCh];
+        RowAcc<T> acc[kMaxCh];
         const T* xi = x + i * ld + col0;
 #pragma unroll
-        for (int c = 0; c < kMaxCh; ++c) acc[c] = c < ch ? d * ld_as_double(xi + c) : 0.0;
+        for (int c = 0; c < kMaxCh; ++c) acc[c].init(c < ch ? dv * __ldg(xi + c) : (T)0);
         for (int l = 0; l < H.nl; ++l) {
             uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
             const uint64_t pm = 1ull | (1ull << H.dist[l]);
+            const T au = cf<T>(__ldg(H.KA + kMaxLayers + l), __ldg(H.KAf + kMaxLayers + l));
             while (o) {
                 int p = __ffsll((long long)o) - 1;
                 o &= o - 1;
                 uint64_t s2 = s ^ (pm << p);
                 uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
-                double amp = H.apos[l] < 0 ? H.A[l] : H.pos[H.apos[l] + p];
+                const T amp = H.apos[l] < 0 ? au : posT[H.apos[l] + p];
                 const T* xj = x + j * ld + col0;
 #pragma unroll
                 for (int c = 0; c < kMaxCh; ++c)
-                    if (c < ch) acc[c] += amp * ld_as_double(xj + c);
+                    if (c < ch) acc[c].add(amp * __ldg(xj + c));
             }
         }
         T* yi = y + i * ld + col0;
 #pragma unroll
         for (int c = 0; c < kMaxCh; ++c)
-            if (c < ch) yi[c] = (T)acc[c];
+            if (c < ch) yi[c] = acc[c].get();
     }
 }
 
@@ -122,24 +157,30 @@ __global__ void __launch_bounds__(256) k_matvec_qg(DevSector S, DevTermsQG H, co
     stage_os(S, sm, use_sm, off_s, str_s);
     const int Q = S.Q;
     const uint64_t dm = (1ull << S.nb) - 1;
+    const T* siteT = sizeof(T) == 8 ? (const T*)H.site_f : (const T*)H.site_ff;
+    const T* pairT = sizeof(T) == 8 ? (const T*)H.pair_K : (const T*)H.pair_Kf;
+    const T* hopT = sizeof(T) == 8 ? (const T*)H.hop_t : (const T*)H.hop_tf;
+    const T* ampT = sizeof(T) == 8 ? (const T*)H.amp : (const T*)H.ampf;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = d_unrank(S, off_s, str_s, i);
-        double d = H.C;
+        RowAcc<T> d;
+        d.init(cf<T>(H.C, H.Cf));
         for (int q = 0; q < H.nsite; ++q) {
             int n = (int)((s >> H.site_sh[q]) & dm);
-            d += H.site_f[q * Q + n];
+            d.add(siteT[q * Q + n]);
         }
         for (int q = 0; q < H.npair; ++q) {
             int a = (int)((s >> H.pair_sh[2 * q]) & dm), b = (int)((s >> H.pair_sh[2 * q + 1]) & dm);
-            d += H.pair_K[q] * (double)(a * b);
+            if (a * b) d.add(pairT[q] * (T)(a * b));
         }
-        double acc[kMaxCh];
+        const T dv = d.get();
+        RowAcc<T> acc[kMaxCh];
         const T* xi = x + i * ld + col0;
 #pragma unroll
-        for (int c = 0; c < kMaxCh; ++c) acc[c] = c < ch ? d * ld_as_double(xi + c) : 0.0;
+        for (int c = 0; c < kMaxCh; ++c) acc[c].init(c < ch ? dv * __ldg(xi + c) : (T)0);
         for (int q = 0; q < H.nhop; ++q) {
             const int sa = H.hop_sh[2 * q], sb = H.hop_sh[2 * q + 1];
-            const double t = H.hop_t[q];
+            const T t = hopT[q];
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
                 const int s_up = dir ? sb : sa, s_dn = dir ? sa : sb;  // b+_up b_dn
@@ -147,18 +188,18 @@ __global__ void __launch_bounds__(256) k_matvec_qg(DevSector S, DevTermsQG H, co
                 if (nu < Q - 1 && nd > 0) {
                     uint64_t s2 = s + (1ull << s_up) - (1ull << s_dn);
                     uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
-                    double amp = -t * H.amp[nu * Q + nd];
+                    const T amp = -t * ampT[nu * Q + nd];
                     const T* xj = x + j * ld + col0;
 #pragma unroll
                     for (int c = 0; c < kMaxCh; ++c)
-                        if (c < ch) acc[c] += amp * ld_as_double(xj + c);
+                        if (c < ch) acc[c].add(amp * __ldg(xj + c));
                 }
             }
         }
         T* yi = y + i * ld + col0;
 #pragma unroll
         for (int c = 0; c < kMaxCh; ++c)
-            if (c < ch) yi[c] = (T)acc[c];
+            if (c < ch) yi[c] = acc[c].get();
     }
 }
 

@@ -56,6 +56,7 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     for (int p = 1; p < L; ++p)
         if (lin[p] != lin[0]) uniform_lin = false;
     std::vector<double> pos;  // per-position tables, 64 entries each
+    double Kh[kMaxLayers] = {0}, Ah[kMaxLayers] = {0};
     std::vector<double> lin_host;
     if (uniform_lin) {
         C += lin[0] * s->N;  // sum_p lin sigma_p = lin * N on the sector
@@ -82,8 +83,8 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
                 v.dist[nl] = d;
                 v.dmask[nl] = g.first.first != 0.0 ? g.second : 0;
                 v.omask[nl] = g.first.second != 0.0 ? g.second : 0;
-                v.K[nl] = g.first.first;
-                v.A[nl] = g.first.second;
+                Kh[nl] = g.first.first;
+                Ah[nl] = g.first.second;
                 v.kpos[nl] = -1;
                 v.apos[nl] = -1;
                 ++nl;
@@ -117,15 +118,34 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         int rc = build_panel_plan(s, C, uniform_lin, plist, t);
         if (rc) return rc;
     }
+    v.Cf = (float)v.C;
+    std::vector<float> kaf(2 * kMaxLayers, 0.f);
+    std::vector<double> ka(2 * kMaxLayers, 0.0);
+    for (int l = 0; l < nl; ++l) {
+        ka[l] = Kh[l];
+        ka[kMaxLayers + l] = Ah[l];
+        kaf[l] = (float)Kh[l];
+        kaf[kMaxLayers + l] = (float)Ah[l];
+    }
     int rc;
     void* p;
+    if ((rc = dev_upload(t->dev_allocs, ka.data(), ka.size() * 8, &p))) return rc;
+    v.KA = (const double*)p;
+    if ((rc = dev_upload(t->dev_allocs, kaf.data(), kaf.size() * 4, &p))) return rc;
+    v.KAf = (const float*)p;
     if (!lin_host.empty()) {
         if ((rc = dev_upload(t->dev_allocs, lin_host.data(), 64 * 8, &p))) return rc;
         v.lin = (const double*)p;
+        std::vector<float> lf(lin_host.begin(), lin_host.end());
+        if ((rc = dev_upload(t->dev_allocs, lf.data(), lf.size() * 4, &p))) return rc;
+        v.linf = (const float*)p;
     }
     if (!pos.empty()) {
         if ((rc = dev_upload(t->dev_allocs, pos.data(), pos.size() * 8, &p))) return rc;
         v.pos = (const double*)p;
+        std::vector<float> pf(pos.begin(), pos.end());
+        if ((rc = dev_upload(t->dev_allocs, pf.data(), pf.size() * 4, &p))) return rc;
+        v.posf = (const float*)p;
     }
     return DQ_OK;
 }
@@ -198,6 +218,18 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     v.hop_t = (const double*)p;
     if ((rc = dev_upload(t->dev_allocs, amp.data(), amp.size() * 8, &p))) return rc;
     v.amp = (const double*)p;
+    v.Cf = (float)v.C;
+    auto upf = [&](const std::vector<double>& src, const float** dst) -> int {
+        std::vector<float> f(src.begin(), src.end());
+        void* q;
+        int r = dev_upload(t->dev_allocs, f.data(), f.size() * 4, &q);
+        *dst = (const float*)q;
+        return r;
+    };
+    if ((rc = upf(site_f, &v.site_ff))) return rc;
+    if ((rc = upf(pair_K, &v.pair_Kf))) return rc;
+    if ((rc = upf(hop_t, &v.hop_tf))) return rc;
+    if ((rc = upf(amp, &v.ampf))) return rc;
     return DQ_OK;
 }
 
