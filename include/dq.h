@@ -226,6 +226,22 @@ void dq_batch_free(dq_batch* b);
 int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0, int steps, int dtype, int reorth,
                double* E0, double* alpha, double* beta, int* steps_done, void* stream);
 
+/* ---- kernel timing ------------------------------------------------------------------------ */
+
+/* Measurement hooks; the paper has no counterpart. While timing is on, every dq_matvec,
+ * dq_matvec_noalloc and dq_batch_matvec call records a pair of CUDA events on its own stream
+ * around its main kernel (the panel kernel, the general product kernel or the batched kernel) and
+ * counts the kernels the call launched (the panel path launches three: two prepass kernels and
+ * the panel kernel). Calls made while the stream is being captured into a CUDA graph are neither
+ * timed nor counted. dq_timing_enable(1) turns timing on and clears the record;
+ * dq_timing_enable(0) turns it off and keeps the record. dq_timing_read waits for the recorded
+ * events and returns (each pointer may be NULL) the summed main-kernel time in milliseconds, the
+ * number of product calls counted and the number of kernels they launched. At most 65536 calls
+ * are timed after a reset; later ones are counted but not timed, and dq_timing_read then returns
+ * DQ_ERANGE along with the partial sums. Thread-safe. Errors: DQ_ECUDA. */
+int dq_timing_enable(int on);
+int dq_timing_read(double* ms, long long* launches, long long* kernels);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,7 @@ EXPORTED = (
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
     "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_matvec_noalloc",
     "dq_lanczos", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free", "dq_term_grads",
+    "dq_timing_enable", "dq_timing_read",
 )
 
 
@@ -71,6 +72,8 @@ def _load() -> ctypes.CDLL:
         "dq_term_grads": (i32, [vp, P(_Term), i32, vp, vp, i32, i32, vp, vp]),
         "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
                              P(ctypes.c_double), P(i32), vp]),
+        "dq_timing_enable": (i32, [i32]),
+        "dq_timing_read": (i32, [P(ctypes.c_double), P(ctypes.c_longlong), P(ctypes.c_longlong)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -350,3 +353,15 @@ def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True) -
                            1 if reorth else 0, ctypes.byref(E0), alpha, beta, ctypes.byref(done), _stream_handle()))
     m = done.value
     return {"E0": E0.value, "alpha": np.array(alpha[:m]), "beta": np.array(beta[:m]), "steps_done": m}
+
+
+def timing_enable(on: bool = True):
+    """Turn the main-kernel timing hooks on (clearing the record) or off."""
+    _check(_lib.dq_timing_enable(1 if on else 0))
+
+
+def timing_read():
+    """(main-kernel milliseconds, product calls, kernels launched) since the last timing_enable(True)."""
+    ms, n, k = ctypes.c_double(), ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.dq_timing_read(ctypes.byref(ms), ctypes.byref(n), ctypes.byref(k)))
+    return ms.value, n.value, k.value

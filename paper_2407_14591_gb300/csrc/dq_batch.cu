@@ -203,10 +203,12 @@ static int batch_launch(dq_batch* b, const void* const* x, void* const* y, cudaS
     bp.total_tiles = t;
     unsigned long long cap = (unsigned long long)sm_count() * sh.per_sm;
     unsigned grid = (unsigned)(t < cap ? (t ? t : 1) : cap);
+    const int tslot = timing_start(st);
     if (b->dtype == DQ_F64)
         k_batch<double><<<grid, sh.threads, 0, st>>>(bp);
     else
         k_batch<float><<<grid, sh.threads, 0, st>>>(bp);
+    timing_stop(tslot, st, 1);
     return (int)cudaGetLastError();
 }
 

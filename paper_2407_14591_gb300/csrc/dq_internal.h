@@ -6,6 +6,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/dq.h"
 
 namespace dq {
@@ -191,6 +193,12 @@ int launch_panel_matvec(const dq_sector* s, dq_terms* t, const void* x, void* y,
 size_t panel_scratch_bytes(const dq_sector* s, int dtype);
 int launch_panel_matvec_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* scratch,
                            void* stream);
+
+// kernel timing (dq_timing.cpp): timing_start records the start event of a main kernel on `st`
+// and returns its slot (-1: timing off or stream capturing); timing_stop records the stop event
+// and counts the call's `kernels` launches
+int timing_start(cudaStream_t st);
+void timing_stop(int slot, cudaStream_t st, int kernels);
 
 // device memory helpers; without a CUDA device dev_upload returns DQ_OK and a NULL pointer
 bool device_present();

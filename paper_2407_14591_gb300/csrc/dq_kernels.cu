@@ -242,6 +242,7 @@ static int launch_matvec_t(const dq_sector* s, const dq_terms* t, const T* x, T*
     size_t smb = sm ? os_bytes(S) : 0;
     bool lin2 = (S.n_sub == 2);
     unsigned grid = grid_for(S.D, 256, 8);
+    const int tslot = timing_start(st);
     for (int c0 = 0; c0 < nrhs; c0 += kMaxCh) {
         int ch = nrhs - c0 < kMaxCh ? nrhs - c0 : kMaxCh;
         if (t->q2) {
@@ -256,6 +257,7 @@ static int launch_matvec_t(const dq_sector* s, const dq_terms* t, const T* x, T*
                 k_matvec_qg<T, false><<<grid, 256, smb, st>>>(S, t->qgv, x, y, nrhs, c0, ch, sm);
         }
     }
+    timing_stop(tslot, st, (nrhs + kMaxCh - 1) / kMaxCh);
     return (int)cudaGetLastError();
 }
 

@@ -8,21 +8,24 @@
 // x to 2^-F, at most 2^-57 (FP64) or 2^-31 (FP32) of max|x| per term.
 //
 // Data movement. One CTA per panel (all rows with one P_0 pattern s0, contiguous in the
-// canonical order). The panel of x is copied to shared memory with a bulk TMA copy; hops inside
-// P_1 are shared-memory gathers through the P_1 rank table (also in shared memory); hops inside
-// P_0 read the partner panel element by element (coalesced); hops across the cut read the panel
-// s0 ^ bit_a of the neighbouring block, double-buffered in shared memory by bulk copies. Every
-// y element is written once, by one thread.
+// canonical order), persistent over panels. The panel of x is loaded into shared memory; hops
+// inside P_1 are shared-memory gathers through the P_1 rank table (also in shared memory); hops
+// inside P_0 read the partner panel element by element (coalesced); hops across the cut read the
+// panel s0 ^ bit_a of the neighbouring block from a ring of shared-memory slots filled by bulk
+// (TMA) copies, two in flight for FP64 and five for FP32. The last warp done with a slot starts
+// its next copy, so the warps never wait for each other inside a panel. Gathers of inactive hops
+// are not skipped but pointed at a slot that holds zero: no branches, and all such lanes read one
+// address. Every y element is written once, by one thread.
 #include <cstdint>
 
 #include <cuda_runtime.h>
 
 #include "dq_internal.h"
 
+
 namespace dq {
 
 constexpr int kPT = 1024;  // threads per panel CTA
-constexpr int kEPT = 7;    // rows per thread: panels up to 7168 rows (C(15,7) = 6435)
 constexpr unsigned kWaitLimit = 1u << 22;
 
 template <typename T>
@@ -187,17 +190,26 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-// Bounded wait for phase `parity` of `bar`; false if the limit was reached.
-__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool bar_try(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait for phase `parity` of `bar`. On timeout it raises the block's abort flag, after
+// which every wait of the block returns false at once: a lost copy costs one time limit, not one
+// per wait.
+__device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+    if (*abort_flag) return false;
     for (unsigned it = 0; it < kWaitLimit; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-            : "=r"(done)
-            : "r"(smem_addr(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
+        if (bar_try(bar, parity)) return true;
+        if ((it & 63u) == 63u && *abort_flag) return false;
     }
+    *abort_flag = 1;
     return false;
 }
 
@@ -215,17 +227,25 @@ __device__ __forceinline__ int stage(XT* buf, const XT* X, uint64_t start, int l
 
 // ------------------------------------------------------------------ panel kernel -------------
 
-// Shared-memory layout of the panel kernel. The P_1 rank table sits at offset 0 and holds byte
-// offsets (local index * sizeof(XT)), so a gather is two loads with no address arithmetic: the
-// table entry at (s1 ^ pair) * 2 and the panel element at kOwn + entry.
-constexpr int kT1Bytes = 65536;  // 2^15 entries of 2 bytes
-constexpr int kOwn = kT1Bytes;   // the panel's own buffer starts here
+// Shared-memory layout of the panel kernel:
+//   [0, kT1Bytes)  the P_1 rank table (local index of every pattern, as a byte offset) and, at
+//                  kZeroSlot, one entry that points at a zero element;
+//   kOwn + s * bstride, s < R: R slots of cap + 8 elements. Slot 0 holds the panel's own x, slots
+//                  1 .. R-1 are the ring of cut partners. Elements cap - 1 .. cap + 6 of every
+//                  slot stay zero (no copy reaches them).
+//   then R mbarriers and the panel's source list.
+// A table entry is a byte offset into a slot, so a gather is two loads with no address arithmetic.
+constexpr int kT1Entries = 1 << 15;
+constexpr uint32_t kZeroSlot = 2 * kT1Entries;  // byte offset of the zero-slot entry
+constexpr int kT1Bytes = 2 * kT1Entries + 128;
+constexpr int kOwn = kT1Bytes;
+constexpr int kZeroPad = 8;
 template <typename XT>
 struct PanelSmem {
     static __host__ __device__ size_t al(size_t b) { return (b + 127) & ~(size_t)127; }
-    static __host__ __device__ size_t buf_bytes(int cap) { return al((size_t)cap * sizeof(XT)); }
-    static __host__ __device__ size_t total(int cap, int nstg) {
-        return kT1Bytes + (size_t)(1 + nstg) * buf_bytes(cap) + 128 + 8 * kPanelMaxList;
+    static __host__ __device__ size_t buf_bytes(int cap) { return al((size_t)(cap + kZeroPad) * sizeof(XT)); }
+    static __host__ __device__ size_t total(int cap, int nslots) {
+        return kT1Bytes + (size_t)nslots * buf_bytes(cap) + 128 + 8 * kPanelMaxList;
     }
 };
 
@@ -250,15 +270,53 @@ struct PanelCtx {
     int n1, C, ncls0, np0, nx;
 };
 
-// All the work of one panel for rows tid + e * kPT, e < E. Rows past the panel hold s = 0: no
-// pair inside P_1 is active for them, cut hops read harmless in-range entries, and they are
-// never stored.
-template <typename XT, typename OUT, int NA, int NSTG, int E>
+// Block-shared bookkeeping of the copy ring.
+template <int R>
+struct Ring {
+    int done[R];   // warps finished with each slot's current contents
+    int issued[R]; // copies started into each slot (for the drain after a timeout)
+    int abort;     // a wait timed out
+};
+
+// Start the copy of cut partner j (entry np0 + j of the source list) into slot s.
+template <typename XT, int R>
+__device__ __forceinline__ void issue_cut(int j, int s, const PanelPlan& P, const PanelCtx& pc, const XT* X,
+                                          unsigned char* smem, size_t bstride, uint64_t* bar, const uint64_t* lst,
+                                          Ring<R>& rg) {
+    const uint64_t ent = lst[pc.np0 + j];
+    const int g = (int)(ent >> 48);
+    const int len = (int)P.t1len[pc.n1 + ((pc.s0 & P.xg_abit[g]) ? 1 : -1)];
+    stage(reinterpret_cast<XT*>(smem + kOwn + s * bstride), X, ent & ((1ull << 48) - 1), len, &bar[s]);
+    rg.issued[s] += 1;
+}
+
+// Every warp calls this when it has finished reading slot s; the last of the block's warps
+// starts the copy of cut partner jn into it (if there is one). No block-wide barrier: the other
+// warps go on with their next slot.
+template <typename XT, int R>
+__device__ __forceinline__ void release_slot(int s, int jn, const PanelPlan& P, const PanelCtx& pc, const XT* X,
+                                             unsigned char* smem, size_t bstride, uint64_t* bar, const uint64_t* lst,
+                                             Ring<R>& rg) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();  // this warp's reads of the slot happen before the count
+        if (atomicAdd(&rg.done[s], 1) == kPT / 32 - 1) {
+            rg.done[s] = 0;
+            __threadfence_block();
+            if (jn < pc.nx && !rg.abort) issue_cut<XT, R>(jn, s, P, pc, X, smem, bstride, bar, lst, rg);
+        }
+    }
+}
+
+// All the work of one panel for rows tid + e * kPT, e < E. Rows past the panel hold s = 0: their
+// gathers read in-range entries, and they are never stored.
+template <typename XT, typename OUT, int NA, int R, int E>
 __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restrict__ X, OUT* __restrict__ y,
                                            unsigned char* smem, uint64_t* bar, const uint64_t* lst, const PanelDiag& dg,
-                                           const PanelCtx& pc, size_t bstride, uint32_t& ph_stg, int scale, int& fail) {
+                                           const PanelCtx& pc, size_t bstride, uint32_t& ph, int scale, int& fail,
+                                           Ring<R>& rg) {
     const int tid = threadIdx.x;
-    const XT* own = reinterpret_cast<const XT*>(smem + kOwn);
+    const unsigned char* own = smem + kOwn;
     uint32_t s2[E];  // P_1 pattern of each row, shifted left by one (rank-table byte offset)
     long long acc[NA][E];
     const uint16_t* st = P.t1states + P.t1start[pc.n1];
@@ -293,7 +351,9 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
             }
         }
     }
-    // hops inside P_1, layer by layer: a = s ^ (s >> d) marks the active pairs of the layer
+    // hops inside P_1, layer by layer: a = s ^ (s >> d) marks the active pairs of the layer; rows
+    // whose pair is not active read the zero slot (one address for all of them, so no bank
+    // conflicts and no branch)
     for (int l = 0; l < P.n_p1l; ++l) {
         const int d = P.p1l_d[l];
         uint32_t a[E];
@@ -305,24 +365,24 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
             for (int q = q0; q < q1; ++q) {
                 const uint32_t lb = P.p1b_lobit[q] << 1, pm2 = P.p1b_pm2[q];
 #pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (a[e] & lb) acc[k][e] += lds_x<XT>(smem + kOwn, lds_u16(smem, s2[e] ^ pm2));
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t t = (a[e] & lb) ? (s2[e] ^ pm2) : kZeroSlot;
+                    acc[k][e] += lds_x<XT>(own, lds_u16(smem, t));
+                }
             }
         }
     }
-    // hops across the cut: panel s0 ^ bit_a of the neighbouring block, NSTG copies in flight
+    // hops across the cut: panel s0 ^ bit_a of the neighbouring block, in the copy ring
     for (int j = 0; j < pc.nx; ++j) {
-        const int b = j % NSTG;
-        if (!bar_wait(&bar[1 + b], (ph_stg >> b) & 1u)) fail = 1;
-        ph_stg ^= 1u << b;
+        const int s = 1 + j % (R - 1);
+        if (!bar_wait(&bar[s], (ph >> s) & 1u, &rg.abort)) fail = 1;
+        ph ^= 1u << s;
         const uint64_t ent = lst[pc.np0 + j];
         const int g = (int)(ent >> 48);
-        const unsigned char* sp = smem + kOwn + (1 + b) * bstride + (ent & (16 / sizeof(XT) - 1)) * sizeof(XT);
-        // a hop needs s_b != s_a: with s_a = 1 the particle moves a -> b (b empty)
+        const unsigned char* sp = smem + kOwn + s * bstride + (ent & (16 / sizeof(XT) - 1)) * sizeof(XT);
+        // a hop needs s_b != s_a: with s_a = 1 the particle moves a -> b (b empty); rows whose
+        // pair is not active read the zero slot
         const uint32_t flip = (pc.s0 & P.xg_abit[g]) ? ~0u : 0u;
-        uint32_t sx[E];
-#pragma unroll
-        for (int e = 0; e < E; ++e) sx[e] = s2[e] ^ flip;
 #pragma unroll
         for (int k = 0; k < NA; ++k) {
             const int b0 = k ? P.xg_cut[g] : P.xg_first[g];
@@ -330,17 +390,13 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
             for (int q = b0; q < b1; ++q) {
                 const uint32_t bb2 = P.xb_bit[q] << 1;
 #pragma unroll
-                for (int e = 0; e < E; ++e)
-                    if (sx[e] & bb2) acc[k][e] += lds_x<XT>(sp, lds_u16(smem, s2[e] ^ bb2));
+                for (int e = 0; e < E; ++e) {
+                    const uint32_t t = ((s2[e] ^ flip) & bb2) ? (s2[e] ^ bb2) : kZeroSlot;
+                    acc[k][e] += lds_x<XT>(sp, lds_u16(smem, t));
+                }
             }
         }
-        __syncthreads();  // buffer b is free again
-        if (tid == 0 && j + NSTG < pc.nx) {
-            const uint64_t e2 = lst[pc.np0 + j + NSTG];
-            const int g2 = (int)(e2 >> 48);
-            const int len = (int)P.t1len[pc.n1 + ((pc.s0 & P.xg_abit[g2]) ? 1 : -1)];
-            stage(reinterpret_cast<XT*>(smem + kOwn + (1 + b) * bstride), X, e2 & ((1ull << 48) - 1), len, &bar[1 + b]);
-        }
+        release_slot<XT, R>(s, j + R - 1, P, pc, X, smem, bstride, bar, lst, rg);
     }
     // the row result: (C + sum_k K_k n_k) x_i + sum_k A_k S_k, exactly, rounded once
     const uint32_t m1 = (1u << P.L1) - 1u;
@@ -361,14 +417,14 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
             md += P.MK[k] * n;
         }
         I128 r = {0, 0};
-        mac(r, md, (long long)own[c]);
+        mac(r, md, lds_x<XT>(own, (uint32_t)(c * sizeof(XT))));
 #pragma unroll
         for (int k = 0; k < NA; ++k) mac(r, P.MA[k], acc[k][e]);
         y[pc.start + c] = i128_to<OUT>(r, scale);
     }
 }
 
-template <typename XT, typename OUT, int NA, int NSTG>
+template <typename XT, typename OUT, int NA, int R>
 __global__ void __launch_bounds__(kPT, 1)
     k_panel(PanelPlan P, const XT* __restrict__ X, OUT* __restrict__ y, const WsHeader* __restrict__ h, int* err,
             int cap) {
@@ -378,26 +434,35 @@ __global__ void __launch_bounds__(kPT, 1)
     uint16_t* t1 = reinterpret_cast<uint16_t*>(smem);
     XT* own = reinterpret_cast<XT*>(smem + kOwn);
     const size_t bstride = SL::buf_bytes(cap);
-    unsigned char* tail = smem + kOwn + (size_t)(1 + NSTG) * bstride;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(tail);  // [1 + b]: staging buffer b
+    unsigned char* tail = smem + kOwn + (size_t)R * bstride;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(tail);  // [s]: copy slot s
     uint64_t* lst = reinterpret_cast<uint64_t*>(tail + 128);
     __shared__ uint32_t s_hdr;
     __shared__ int s_fail;
     __shared__ PanelDiag dg;
+    __shared__ Ring<R> rg;
+    const uint16_t zoff = (uint16_t)((cap - 1) * sizeof(XT));  // byte offset of a zero element
 
-    for (int q = tid; q < (1 << P.L1); q += kPT) t1[q] = (uint16_t)(P.t1rank[q] * sizeof(XT));
     if (tid == 0) {
-        for (int b = 1; b <= NSTG; ++b) bar_init(&bar[b]);
+        for (int s = 0; s < R; ++s) {
+            bar_init(&bar[s]);
+            rg.done[s] = 0;
+            rg.issued[s] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        rg.abort = 0;
         s_fail = 0;
+        t1[kT1Entries] = zoff;
     }
+    if (tid < kZeroPad * R) reinterpret_cast<XT*>(smem + kOwn + (tid / kZeroPad) * bstride)[cap - 1 + tid % kZeroPad] = 0;
+    for (int q = tid; q < (1 << P.L1); q += kPT) t1[q] = (uint16_t)(__ldg(P.t1rank + q) * sizeof(XT));
     __syncthreads();
     if (h->bad) {  // non-finite x: y is left unwritten and the error word is raised
         if (blockIdx.x == 0 && tid == 0) atomicAdd(err, 1);
         return;
     }
     const int scale = P.emin - h->F;
-    uint32_t ph_stg = 0u;  // mbarrier parity of each staging buffer (bit b)
+    uint32_t ph = 0u;  // mbarrier parity of each slot (bit s)
     int fail = 0;
 
     for (uint32_t pi = blockIdx.x; pi < P.npanels; pi += gridDim.x) {
@@ -406,7 +471,7 @@ __global__ void __launch_bounds__(kPT, 1)
         pc.start = P.panel_start[pi];
         pc.n1 = P.N - __popc(pc.s0);
         pc.C = (int)P.t1len[pc.n1];
-        // warp 0: source list into shared memory and the first copies; warp 1: diagonal counters
+        // warp 0: source list into shared memory and the first copies; warps 1..: diagonal counters
         if (tid < 32) {
             const uint32_t lo = __ldg(P.list_off + pi), hi = __ldg(P.list_off + pi + 1);
             for (uint32_t q = lo + tid; q < hi; q += 32) lst[q - lo] = __ldg(P.list + q);
@@ -414,14 +479,11 @@ __global__ void __launch_bounds__(kPT, 1)
             __syncwarp();
             if (tid == 0) {
                 const uint32_t hd = s_hdr;
-                const int np0 = (int)(hd & 255u) + (int)((hd >> 8) & 255u), nx = (int)((hd >> 16) & 255u);
-                for (int j = 0; j < nx && j < NSTG; ++j) {
-                    const uint64_t ent = lst[np0 + j];
-                    const int g = (int)(ent >> 48);
-                    const int len = (int)P.t1len[pc.n1 + ((pc.s0 & P.xg_abit[g]) ? 1 : -1)];
-                    stage(reinterpret_cast<XT*>(smem + kOwn + (1 + j) * bstride), X, ent & ((1ull << 48) - 1), len,
-                          &bar[1 + j]);
-                }
+                PanelCtx pq = pc;
+                pq.np0 = (int)(hd & 255u) + (int)((hd >> 8) & 255u);
+                pq.nx = (int)((hd >> 16) & 255u);
+                for (int j = 0; j < pq.nx && j < R - 1; ++j)
+                    issue_cut<XT, R>(j, 1 + j, P, pq, X, smem, bstride, bar, lst, rg);
             }
         } else if (tid < 32 + kPanelMaxK) {
             const int k = tid - 32;
@@ -453,7 +515,7 @@ __global__ void __launch_bounds__(kPT, 1)
                 dg.w1[k][q] = w1[q];
             }
         }
-        // the panel's own x: plain coalesced loads into its buffer (element c at kOwn + c*size)
+        // the panel's own x: plain coalesced loads into slot 0 (element c at kOwn + c*size)
         {
             const XT* src = X + pc.start;
             for (int c = tid; c < pc.C; c += kPT) own[c] = __ldg(src + c);
@@ -465,18 +527,25 @@ __global__ void __launch_bounds__(kPT, 1)
         pc.nx = (int)((hd >> 16) & 255u);
         const int ne = (pc.C + kPT - 1) / kPT;
         if (ne > 4)
-            panel_rows<XT, OUT, NA, NSTG, 7>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+            panel_rows<XT, OUT, NA, R, 7>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
         else if (ne > 2)
-            panel_rows<XT, OUT, NA, NSTG, 4>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+            panel_rows<XT, OUT, NA, R, 4>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
         else if (ne == 2)
-            panel_rows<XT, OUT, NA, NSTG, 2>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+            panel_rows<XT, OUT, NA, R, 2>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
         else
-            panel_rows<XT, OUT, NA, NSTG, 1>(P, X, y, smem, bar, lst, dg, pc, bstride, ph_stg, scale, fail);
+            panel_rows<XT, OUT, NA, R, 1>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
         __syncthreads();
     }
     if (fail) s_fail = 1;
     __syncthreads();
-    if (tid == 0 && s_fail) atomicAdd(err, 1);
+    if (tid == 0 && (s_fail || rg.abort)) {
+        atomicAdd(err, 1);
+        // after a timeout, wait (bounded) for the copies still in flight before the block exits
+        for (int s = 0; s < R; ++s)
+            if (rg.issued[s] > 0)
+                for (unsigned it = 0; it < kWaitLimit && !bar_try(&bar[s], (uint32_t)(rg.issued[s] - 1) & 1u); ++it) {
+                }
+    }
 }
 
 // ------------------------------------------------------------------ launch -------------------
@@ -497,7 +566,7 @@ static int sms_count() {
     return sms;
 }
 
-template <typename T, typename XT, int NA, int NSTG>
+template <typename T, typename XT, int NA, int R>
 static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {
     const PanelPlan& P = t->pp;
     WsHeader* h = reinterpret_cast<WsHeader*>(ws);
@@ -507,19 +576,22 @@ static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, vo
     k_exp_max<T><<<sms * 4, 256, 0, st>>>(x, s->D, h);
     k_to_fixed<T, XT><<<sms * 8, 256, 0, st>>>(x, X, s->D, h);
     const int cap = P.cmax + 16 / (int)sizeof(XT) + 4;
-    size_t sm = PanelSmem<XT>::total(cap, NSTG);
-    auto kern = k_panel<XT, T, NA, NSTG>;
+    size_t sm = PanelSmem<XT>::total(cap, R);
+    auto kern = k_panel<XT, T, NA, R>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
     unsigned grid = (unsigned)(P.npanels < (uint32_t)sms ? P.npanels : (uint32_t)sms);
+    const int tslot = timing_start(st);
     kern<<<grid, kPT, sm, st>>>(P, X, y, h, s->dev.err, cap);
+    timing_stop(tslot, st, 3);
     return (int)cudaGetLastError();
 }
 
 template <typename T, typename XT, int NA>
 static int run_panel_n(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {
-    // staging depth that fits next to the rank table and the panel's own buffer (227 KB)
-    return run_panel<T, XT, NA, sizeof(XT) == 8 ? 2 : 5>(s, t, x, y, ws, st);
+    // copy slots (the panel's own buffer and the staging buffers) that fit next to the rank
+    // table in 227 KB of shared memory
+    return run_panel<T, XT, NA, sizeof(XT) == 8 ? 3 : 6>(s, t, x, y, ws, st);
 }
 
 int launch_panel_matvec_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,

@@ -122,3 +122,11 @@ def test_device_calls_fail_loudly_without_gpu():
     assert rc == b.DQ_ECUDA and b"no CUDA device" in lib.dq_last_error()
     rc = lib.dq_state_at_batch(s.handle, x, y, 4, None)
     assert rc == b.DQ_ECUDA
+
+
+def test_timing_hooks_without_products():
+    """dq_timing_*: enabling clears the record; with no product call nothing is timed or counted."""
+    b.timing_enable(True)
+    assert b.timing_read() == (0.0, 0, 0)
+    b.timing_enable(False)
+    assert b.timing_read() == (0.0, 0, 0)

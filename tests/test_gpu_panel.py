@@ -119,3 +119,26 @@ def test_repeated_calls_and_two_terms_objects():
         r2 = o_matvec(o, wl.heisenberg_terms(wl.chain_bonds(20), 1.0), x)
         assert np.max(np.abs(y1 - r1)) <= 1e-12 * np.max(np.abs(r1))
         assert np.max(np.abs(y2 - r2)) <= 1e-12 * np.max(np.abs(r2))
+
+
+def test_timing_hooks_count_and_time_the_main_kernel():
+    """dq_timing_*: three kernels per panel product, one per general product, positive times."""
+    s = b.make_sector(20, 2, 10, 2)
+    terms = wl.heisenberg_terms(wl.chain_bonds(20), 1.0, 1.0)
+    tp = b.make_terms(s, terms)
+    assert tp.path == "panel"
+    tg = b.make_terms(s, terms + [("Z", 3, -1, 0.3)])  # a non-uniform field leaves the panel path
+    assert tg.path == "general"
+    x = torch.rand(s.dim, dtype=torch.float64, device=DEV)
+    b.matvec(s, tp, x)
+    torch.cuda.synchronize()
+    b.timing_enable(True)
+    for _ in range(3):
+        b.matvec(s, tp, x)
+    b.matvec(s, tg, x)
+    ms, calls, kernels = b.timing_read()
+    b.timing_enable(False)
+    assert calls == 4 and kernels == 3 * 3 + 1
+    assert ms > 0.0
+    b.matvec(s, tp, x)  # timing off: nothing more is recorded
+    assert b.timing_read()[1] == 4
