@@ -38,7 +38,11 @@ FALLBACK_HBM = 6800.0
 
 # DRAM traffic per launch of the product kernel from one ncu capture, keyed by the SHA-256 of the
 # kernel sources it was taken on; reported only while the sources are unchanged.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the full-size product,
+    # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.25 GB read + 1.30 GB written
+    ("j1j2_square_6x5_N15", 2, "f64", 1, "deb0572598321000"): 19.55e9,
+}
 
 WORKLOADS = {
     "j1j2": 2,
@@ -175,6 +179,36 @@ def oracle_rows_rate(w, partition, x, seconds: float, steps: int | None = None, 
     return done / el, done, el, setup, rows_per
 
 
+def lanczos_check(b, torch):
+    """Workload 1 (periodic Heisenberg chain L=20, N=10): 100 Lanczos steps through the library
+    with FP64 and FP32 vectors from the seeded start vector, against the oracle's E0 stored in
+    tests/golden/lanczos_workload1.txt. Wall-clock time of the synchronous call."""
+    from paper_2407_14591_gb300 import workloads as wl
+
+    ref = {}
+    with open(os.path.join(ROOT, "tests", "golden", "lanczos_workload1.txt")) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                ref[line[0]] = line[1]
+    e_ref, steps = float(ref["E0"]), int(ref["steps"])
+    w, _ = wl.workload(1, draw_vector=False)
+    s = b.make_sector(w.L, w.Q, w.N, w.n_sub)
+    w, x = wl.workload(1, D=s.dim)
+    t = b.make_terms(s, w.terms)
+    out = {"workload": w.name, "D": s.dim, "steps": steps, "E0_oracle": e_ref}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        v0 = torch.from_numpy(x).to("cuda", dt)
+        b.lanczos(s, t, v0, steps)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = b.lanczos(s, t, v0, steps)
+        el = time.perf_counter() - t0
+        out[name] = {"E0": r["E0"], "rel_err": abs(r["E0"] - e_ref) / abs(e_ref), "ms": 1e3 * el,
+                     "steps_done": r["steps_done"]}
+    return out
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -256,6 +290,7 @@ def run_batched(args, world, rank, local, dist, torch):
     e1.record(stream)
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
@@ -321,6 +356,7 @@ def run_diff(args, world, rank, local, dist, torch):
     alg_bytes = s.dim * esize * 6
     peak, peak_kind = hbm_peak()
     achieved = alg_bytes / (ms_step / 1e3) / 1e9
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
@@ -393,6 +429,7 @@ def main():
     ap.add_argument("--N", type=int, default=None, help="override the particle number (smaller profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-lanczos", action="store_true", help="skip the workload-1 Lanczos E0 check")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -508,6 +545,8 @@ def main():
                "sample": f"{done} random rows in {el:.1f} s (gather form, numpy single thread), after a "
                          f"{setup:.0f} s untimed sector build"}
 
+    lz = lanczos_check(b, torch) if rank == 0 and not args.no_lanczos else None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
@@ -525,6 +564,7 @@ def main():
             "gpu_launches": kernels,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "lanczos": lz,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

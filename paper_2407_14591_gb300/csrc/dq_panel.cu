@@ -60,23 +60,74 @@ struct WsHeader {
 
 // ------------------------------------------------------------------ prepass -----------------
 
+// Biased exponent field of one element's bits.
+template <typename T>
+__device__ __forceinline__ int exp_field(typename FBits<T>::U b) {
+    return (int)((b >> FBits<T>::MB) & FBits<T>::EMASK);
+}
+
+// x scaled by 2^F and rounded to the integer type XT (round half away from zero).
+template <typename T, typename XT>
+__device__ __forceinline__ XT to_fixed(typename FBits<T>::U b, int F) {
+    using U = typename FBits<T>::U;
+    constexpr int MB = FBits<T>::MB, BIAS = FBits<T>::BIAS;
+    const int e = exp_field<T>(b);
+    unsigned long long m = (unsigned long long)(b & (((U)1 << MB) - 1));
+    int ue;
+    if (e) {
+        m |= 1ull << MB;
+        ue = e - BIAS - MB;
+    } else {
+        ue = 1 - BIAS - MB;
+    }
+    const int sh = ue + F;  // X = m 2^sh
+    unsigned long long v;
+    if (sh >= 0)
+        v = m << sh;
+    else if (sh > -62)
+        v = (m + (1ull << (-sh - 1))) >> (-sh);
+    else
+        v = 0;
+    const long long sv = (b >> (sizeof(U) * 8 - 1)) ? -(long long)v : (long long)v;
+    return (XT)sv;
+}
+
+// Largest biased exponent in x. 16-byte loads when x is 16-byte aligned (the usual case).
 template <typename T>
 __global__ void k_exp_max(const T* __restrict__ x, uint64_t n, WsHeader* h) {
     using U = typename FBits<T>::U;
+    constexpr int V = 16 / sizeof(T);
     int m = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        U b = reinterpret_cast<const U*>(x)[i];
-        int e = (int)((b >> FBits<T>::MB) & FBits<T>::EMASK);
-        m = max(m, e);
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t head = 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const uint4* xv = reinterpret_cast<const uint4*>(x);
+        const uint64_t nv = n / V;
+        for (uint64_t i = t0; i < nv; i += step) {
+            const uint4 q = __ldg(xv + i);
+            if (sizeof(T) == 8) {  // the exponent sits in the high word of each double
+                m = max(m, (int)((q.y >> 20) & 0x7ffu));
+                m = max(m, (int)((q.w >> 20) & 0x7ffu));
+            } else {
+                m = max(m, (int)((q.x >> 23) & 0xffu));
+                m = max(m, (int)((q.y >> 23) & 0xffu));
+                m = max(m, (int)((q.z >> 23) & 0xffu));
+                m = max(m, (int)((q.w >> 23) & 0xffu));
+            }
+        }
+        head = nv * V;
     }
+    for (uint64_t i = head + t0; i < n; i += step) m = max(m, exp_field<T>(reinterpret_cast<const U*>(x)[i]));
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m) atomicMax(&h->emax, m);
 }
 
+// X = round(x 2^F) with F chosen from the largest exponent so that |X| < 2^HEAD. 16-byte loads
+// and stores when x is 16-byte aligned (X always is).
 template <typename T, typename XT>
 __global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t n, WsHeader* h) {
     using U = typename FBits<T>::U;
-    constexpr int MB = FBits<T>::MB, BIAS = FBits<T>::BIAS;
+    constexpr int BIAS = FBits<T>::BIAS;
     const int emax = h->emax;
     if (emax == FBits<T>::EMASK) {  // Inf or NaN in x
         if (blockIdx.x == 0 && threadIdx.x == 0) h->bad = 1;
@@ -85,28 +136,30 @@ __global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t
     // |x| < 2^(emax - BIAS + 1), so X = x 2^F stays below 2^HEAD
     const int F = XHead<XT>::HEAD - (emax - BIAS + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) h->F = F;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        U b = reinterpret_cast<const U*>(x)[i];
-        int e = (int)((b >> MB) & FBits<T>::EMASK);
-        unsigned long long m = (unsigned long long)(b & (((U)1 << MB) - 1));
-        int ue;
-        if (e) {
-            m |= 1ull << MB;
-            ue = e - BIAS - MB;
-        } else {
-            ue = 1 - BIAS - MB;
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t head = 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && sizeof(XT) == sizeof(T)) {
+        // one 16-byte load of x and one 16-byte store of X per step
+        constexpr int V = 16 / sizeof(T);
+        const uint64_t nv = n / V;
+        for (uint64_t i = t0; i < nv; i += step) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(x) + i);
+            uint4 r;
+            if (sizeof(T) == 8) {
+                const unsigned long long v0 =
+                    (unsigned long long)to_fixed<T, XT>((U)(((unsigned long long)q.y << 32) | q.x), F);
+                const unsigned long long v1 =
+                    (unsigned long long)to_fixed<T, XT>((U)(((unsigned long long)q.w << 32) | q.z), F);
+                r = make_uint4((unsigned)v0, (unsigned)(v0 >> 32), (unsigned)v1, (unsigned)(v1 >> 32));
+            } else {
+                r = make_uint4((unsigned)to_fixed<T, XT>((U)q.x, F), (unsigned)to_fixed<T, XT>((U)q.y, F),
+                               (unsigned)to_fixed<T, XT>((U)q.z, F), (unsigned)to_fixed<T, XT>((U)q.w, F));
+            }
+            reinterpret_cast<uint4*>(X)[i] = r;
         }
-        int sh = ue + F;  // X = m 2^sh
-        unsigned long long v;
-        if (sh >= 0)
-            v = m << sh;
-        else if (sh > -62)
-            v = (m + (1ull << (-sh - 1))) >> (-sh);  // round half away from zero
-        else
-            v = 0;
-        long long sv = (b >> (sizeof(U) * 8 - 1)) ? -(long long)v : (long long)v;
-        X[i] = (XT)sv;
+        head = nv * V;
     }
+    for (uint64_t i = head + t0; i < n; i += step) X[i] = to_fixed<T, XT>(reinterpret_cast<const U*>(x)[i], F);
 }
 
 // ------------------------------------------------------------------ 128-bit helpers ---------
@@ -573,7 +626,7 @@ static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, vo
     XT* X = reinterpret_cast<XT*>(reinterpret_cast<char*>(ws) + 256);
     cudaMemsetAsync(h, 0, sizeof(WsHeader), st);
     const int sms = sms_count();
-    k_exp_max<T><<<sms * 4, 256, 0, st>>>(x, s->D, h);
+    k_exp_max<T><<<sms * 8, 256, 0, st>>>(x, s->D, h);
     k_to_fixed<T, XT><<<sms * 8, 256, 0, st>>>(x, X, s->D, h);
     const int cap = P.cmax + 16 / (int)sizeof(XT) + 4;
     size_t sm = PanelSmem<XT>::total(cap, R);

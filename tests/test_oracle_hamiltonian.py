@@ -15,6 +15,7 @@ import pytest
 import scipy.sparse as sp
 
 import oracle.hamiltonian as oh
+from conftest import read_golden
 from oracle import OracleSector, lanczos, matvec, matvec_rows
 from paper_2407_14591_gb300 import workloads as wl
 
@@ -213,3 +214,35 @@ def test_planted_mistakes_are_caught(monkeypatch):
     orig_diag = oh._diag_term
     monkeypatch.setattr(oh, "_diag_term", lambda s, k, i, j, c, w: orig_diag(s, k, i, j, -c if k == "ZZ" else c, w))
     assert not np.allclose(oracle_dense(sec2, t2), ref2, atol=1e-10)
+
+
+def test_lanczos_golden_workload1_matches_sparse_eigensolver():
+    """The stored oracle Lanczos E0 of workload 1 (L = 20 ring, N = 10) equals the smallest
+    eigenvalue of the Heisenberg Hamiltonian built from Kronecker products over the full 2^20
+    space and restricted to the N = 10 sector (ARPACK), independently of the oracle."""
+    import scipy.sparse as sps
+    from scipy.sparse.linalg import eigsh
+
+    rows = dict((r[0], r[1:]) for r in read_golden("lanczos_workload1.txt"))
+    E0 = float(rows["E0"][0])
+    L = 20
+    sz = sps.csr_matrix(np.diag([0.5, -0.5]))
+    splus = sps.csr_matrix(np.array([[0.0, 1.0], [0.0, 0.0]]))
+    sminus = splus.T.tocsr()
+
+    def site_op(op, i):
+        return sps.kron(sps.kron(sps.identity(2 ** i, format="csr"), op, format="csr"),
+                        sps.identity(2 ** (L - 1 - i), format="csr"), format="csr")
+
+    Z = [site_op(sz, i) for i in range(L)]
+    P = [site_op(splus, i) for i in range(L)]
+    M = [site_op(sminus, i) for i in range(L)]
+    H = sps.csr_matrix((2 ** L, 2 ** L))
+    for i in range(L):
+        j = (i + 1) % L
+        H = H + Z[i] @ Z[j] + 0.5 * (P[i] @ M[j] + M[i] @ P[j])
+    pop = np.array([bin(k).count("1") for k in range(2 ** L)])
+    idx = np.flatnonzero(pop == 10)
+    Hs = H[idx][:, idx]
+    ev = eigsh(Hs, k=1, which="SA", tol=1e-13)[0][0]
+    assert abs(E0 - ev) <= 1e-9 * abs(ev)
