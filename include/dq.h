@@ -146,6 +146,12 @@ void dq_free_terms(dq_terms* t);
  * state i contiguous at [i*nrhs, (i+1)*nrhs). y is overwritten; x and y must not overlap.
  * 1 <= nrhs <= 64. Every y[i] is written exactly once by one thread (gather form), so there
  * are no atomics and the result is deterministic. Asynchronous on `stream`.
+ * FP64 vectors with a spin-1/2 (Q = 2) operator are summed exactly in fixed point: each column of
+ * x is scaled by a power of two and rounded to a 57-bit integer, the coefficients share one
+ * power-of-two grid (at least 55 significant bits relative to the largest), and each y[i] is a
+ * 128-bit integer sum rounded once. On those paths an Inf or NaN in x makes y NaN and raises the
+ * sector's error word (DQ_EDEVICE from dq_check_device). The call keeps a scratch area of
+ * D * nrhs * 8 bytes with the terms (allocated on first use).
  * Errors: DQ_EINVAL (NULL pointers, bad dtype or nrhs, terms of another sector). */
 int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
 
@@ -190,9 +196,10 @@ typedef struct dq_batch dq_batch; /* opaque: up to 64 (sector, terms) pairs for 
 /* Plan one launch over n (1..64) Q = 2 sectors of uneven dimension (different L, N, disorder),
  * each with nrhs (1..8) right-hand sides stored as in dq_matvec, of `dtype`. The sectors and
  * terms must outlive the batch. Uploads the n descriptors (synchronous). FP64 vectors accumulate
- * in FP64; FP32 vectors form products in FP32 and sum them with compensated (Neumaier)
- * summation. Errors: DQ_EINVAL (n, nrhs, dtype out of range; terms of another sector; Q != 2),
- * DQ_ENOMEM, DQ_ECUDA. *out is owned by the caller (dq_batch_free). */
+ * in FP64 (the batched product is bound by its gathers of x, so the fixed-point prepass of
+ * dq_matvec would only add traffic); FP32 vectors form products in FP32 and sum them with
+ * compensated (Neumaier) summation. Errors: DQ_EINVAL (n, nrhs, dtype out of range; terms of
+ * another sector; Q != 2), DQ_ENOMEM, DQ_ECUDA. *out is owned by the caller (dq_batch_free). */
 int dq_batch_make(int n, const dq_sector* const* sectors, const dq_terms* const* terms, int nrhs, int dtype,
                   dq_batch** out);
 
@@ -229,10 +236,10 @@ int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0, int steps,
 /* ---- kernel timing ------------------------------------------------------------------------ */
 
 /* Measurement hooks; the paper has no counterpart. While timing is on, every dq_matvec,
- * dq_matvec_noalloc and dq_batch_matvec call records a pair of CUDA events on its own stream
- * around its main kernel (the panel kernel, the general product kernel or the batched kernel) and
- * counts the kernels the call launched (the panel path launches three: two prepass kernels and
- * the panel kernel). Calls made while the stream is being captured into a CUDA graph are neither
+ * dq_matvec_noalloc, dq_batch_matvec and dq_term_grads call records a pair of CUDA events on its
+ * own stream around its main kernel (the panel kernel, the general product kernel, the batched
+ * kernel or the term-gradient kernels) and counts the kernels the call launched (the panel path
+ * launches three: two prepass kernels and the panel kernel). Calls made while the stream is being captured into a CUDA graph are neither
  * timed nor counted. dq_timing_enable(1) turns timing on and clears the record;
  * dq_timing_enable(0) turns it off and keeps the record. dq_timing_read waits for the recorded
  * events and returns (each pointer may be NULL) the summed main-kernel time in milliseconds, the

@@ -152,7 +152,9 @@ extern "C" int dq_term_grads(const dq_sector* s, const dq_term* terms, int n_ter
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_amp, amp.data(), sizeof(double) * amp.size(), cudaMemcpyHostToDevice, st);
     const bool use_sm = (size_t)s->dev.os_total * 16 <= 48 * 1024;
     const size_t smb = use_sm ? (size_t)s->dev.os_total * 16 : 0;
-    for (int t0 = 0; e == cudaSuccess && t0 < n_terms; t0 += kGradChunk) {
+    const int tslot = e == cudaSuccess ? timing_start(st) : -1;
+    int launched = 0;
+    for (int t0 = 0; e == cudaSuccess && t0 < n_terms; t0 += kGradChunk, launched += 2) {
         const int tcnt = n_terms - t0 < kGradChunk ? n_terms - t0 : kGradChunk;
         if (dtype == DQ_F64)
             k_term_grads<double><<<nb, kGradThreads, smb, st>>>(s->dev, (const GradTerm*)d_gt, t0, tcnt,
@@ -165,6 +167,7 @@ extern "C" int dq_term_grads(const dq_sector* s, const dq_term* terms, int n_ter
         k_grad_finish<<<1, tcnt, 0, st>>>((const double*)d_part, nb, d_grads + t0);
         e = cudaGetLastError();
     }
+    timing_stop(tslot, st, launched);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_gt);
     cudaFree(d_amp);

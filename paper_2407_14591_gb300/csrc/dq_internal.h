@@ -60,6 +60,13 @@ struct DevTermsQ2 {
     const float* KAf;  // [2 * kMaxLayers]: K of layer l at l, A of layer l at kMaxLayers + l
     const float* linf;
     const float* posf;
+    // Fixed-point copies used when the vectors are FP64: every coefficient c is M 2^emin with
+    // an integer M (|M| < 2^55 or less, see compile_q2); the same layout as KA, lin and pos
+    int emin;
+    long long MC;
+    const long long* MKA;
+    const long long* Mlin;  // NULL when lin is
+    const long long* Mpos;
 };
 static_assert(sizeof(DevSector) + sizeof(DevTermsQ2) + 64 <= 4096, "product kernel parameters exceed 4 KB");
 

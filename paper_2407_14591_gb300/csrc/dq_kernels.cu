@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include "dq_device.cuh"
+#include "dq_fixed.cuh"
+#include "dq_row_fx.cuh"
 #include "dq_internal.h"
 
 namespace dq {
@@ -148,6 +150,29 @@ __global__ void __launch_bounds__(256) k_matvec_q2(DevSector S, DevTermsQ2 H, co
     }
 }
 
+// y = H x, Q = 2 operator, FP64 vectors in exact fixed point (row_q2_fx). CH: right-hand
+// sides per pass (1, or kMaxCh for nrhs > 1).
+template <bool LIN2, int CH>
+__global__ void __launch_bounds__(256)
+    k_matvec_q2_fx(DevSector S, DevTermsQ2 H, const long long* __restrict__ X, double* __restrict__ y,
+                   const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    if (hdr->bad) {  // an Inf or NaN in x: y is NaN and the error word is raised
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
+            for (int c = 0; c < ch; ++c) y[i * ld + col0 + c] = __longlong_as_double(0x7ff8000000000000ll);
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(S.err, 1);
+        return;
+    }
+    int sc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin - hdr->F[col0 + c] : 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
+        row_q2_fx<CH, LIN2>(S, H, off_s, str_s, i, X, ld, col0, ch, sc, y);
+}
+
 // y = H x, general-Q operator (bosons).
 template <typename T, bool LIN2>
 __global__ void __launch_bounds__(256) k_matvec_qg(DevSector S, DevTermsQG H, const T* __restrict__ x,
@@ -261,9 +286,52 @@ static int launch_matvec_t(const dq_sector* s, const dq_terms* t, const T* x, T*
     return (int)cudaGetLastError();
 }
 
+// FP64 vectors with the Q = 2 operator: column prepass into the terms' scratch, then the
+// fixed-point kernel.
+static int launch_matvec_q2_fx(const dq_sector* s, dq_terms* t, const double* x, double* y, int nrhs,
+                               cudaStream_t st) {
+    const size_t need = kColScaleBytes + (size_t)s->D * nrhs * sizeof(long long);
+    if (t->scratch_bytes < need) {
+        if (t->scratch) cudaFree(t->scratch);
+        t->scratch = nullptr;
+        t->scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&t->scratch, need);
+        if (e != cudaSuccess) return (int)e;
+        t->scratch_bytes = need;
+    }
+    ColScale* h = reinterpret_cast<ColScale*>(t->scratch);
+    long long* X = reinterpret_cast<long long*>(reinterpret_cast<char*>(t->scratch) + kColScaleBytes);
+    launch_col_prepass<double, long long>(x, X, s->D, nrhs, h, num_sms(), st);
+    const DevSector& S = s->dev;
+    const bool sm = os_in_smem(S);
+    const size_t smb = sm ? os_bytes(S) : 0;
+    const bool lin2 = (S.n_sub == 2);
+    const unsigned grid = grid_for(S.D, 256, 8);
+    const int tslot = timing_start(st);
+    int passes = 0;
+    for (int c0 = 0; c0 < nrhs; c0 += kMaxCh, ++passes) {
+        const int ch = nrhs - c0 < kMaxCh ? nrhs - c0 : kMaxCh;
+        if (nrhs == 1) {
+            if (lin2)
+                k_matvec_q2_fx<true, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else
+                k_matvec_q2_fx<false, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+        } else {
+            if (lin2)
+                k_matvec_q2_fx<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else
+                k_matvec_q2_fx<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+        }
+    }
+    timing_stop(tslot, st, 2 + passes);
+    return (int)cudaGetLastError();
+}
+
 int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (t->panel_ok && nrhs == 1) return launch_panel_matvec(s, const_cast<dq_terms*>(t), x, y, dtype, stream);
+    if (dtype == DQ_F64 && t->q2)
+        return launch_matvec_q2_fx(s, const_cast<dq_terms*>(t), (const double*)x, (double*)y, nrhs, st);
     if (dtype == DQ_F64) return launch_matvec_t<double>(s, t, (const double*)x, (double*)y, nrhs, st);
     return launch_matvec_t<float>(s, t, (const float*)x, (float*)y, nrhs, st);
 }

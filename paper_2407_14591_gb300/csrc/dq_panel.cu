@@ -20,6 +20,7 @@
 
 #include <cuda_runtime.h>
 
+#include "dq_fixed.cuh"
 #include "dq_internal.h"
 
 
@@ -27,29 +28,6 @@ namespace dq {
 
 constexpr int kPT = 1024;  // threads per panel CTA
 constexpr unsigned kWaitLimit = 1u << 22;
-
-template <typename T>
-struct FBits;
-template <>
-struct FBits<double> {
-    using U = unsigned long long;
-    static constexpr int MB = 52, EMASK = 0x7ff, BIAS = 1023;
-};
-template <>
-struct FBits<float> {
-    using U = unsigned int;
-    static constexpr int MB = 23, EMASK = 0xff, BIAS = 127;
-};
-template <typename XT>
-struct XHead;
-template <>
-struct XHead<long long> {
-    static constexpr int HEAD = 56;  // |X| <= 2^56: 64 terms still fit in int64
-};
-template <>
-struct XHead<int> {
-    static constexpr int HEAD = 30;
-};
 
 // Workspace header (first 256 bytes of the scratch area).
 struct WsHeader {
@@ -59,38 +37,6 @@ struct WsHeader {
 };
 
 // ------------------------------------------------------------------ prepass -----------------
-
-// Biased exponent field of one element's bits.
-template <typename T>
-__device__ __forceinline__ int exp_field(typename FBits<T>::U b) {
-    return (int)((b >> FBits<T>::MB) & FBits<T>::EMASK);
-}
-
-// x scaled by 2^F and rounded to the integer type XT (round half away from zero).
-template <typename T, typename XT>
-__device__ __forceinline__ XT to_fixed(typename FBits<T>::U b, int F) {
-    using U = typename FBits<T>::U;
-    constexpr int MB = FBits<T>::MB, BIAS = FBits<T>::BIAS;
-    const int e = exp_field<T>(b);
-    unsigned long long m = (unsigned long long)(b & (((U)1 << MB) - 1));
-    int ue;
-    if (e) {
-        m |= 1ull << MB;
-        ue = e - BIAS - MB;
-    } else {
-        ue = 1 - BIAS - MB;
-    }
-    const int sh = ue + F;  // X = m 2^sh
-    unsigned long long v;
-    if (sh >= 0)
-        v = m << sh;
-    else if (sh > -62)
-        v = (m + (1ull << (-sh - 1))) >> (-sh);
-    else
-        v = 0;
-    const long long sv = (b >> (sizeof(U) * 8 - 1)) ? -(long long)v : (long long)v;
-    return (XT)sv;
-}
 
 // Largest biased exponent in x. 16-byte loads when x is 16-byte aligned (the usual case).
 template <typename T>
@@ -160,68 +106,6 @@ __global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t
         head = nv * V;
     }
     for (uint64_t i = head + t0; i < n; i += step) X[i] = to_fixed<T, XT>(reinterpret_cast<const U*>(x)[i], F);
-}
-
-// ------------------------------------------------------------------ 128-bit helpers ---------
-
-struct I128 {
-    long long hi;
-    unsigned long long lo;
-};
-
-__device__ __forceinline__ void mac(I128& a, long long u, long long v) {
-    unsigned long long plo = (unsigned long long)u * (unsigned long long)v;
-    long long phi = __mul64hi(u, v);
-    unsigned long long lo = a.lo + plo;
-    a.hi += phi + (lo < a.lo ? 1 : 0);
-    a.lo = lo;
-}
-
-// Round the integer a * 2^scale to the nearest double / float (ties to even).
-template <typename OUT>
-__device__ __forceinline__ OUT i128_to(I128 a, int scale) {
-    constexpr int P = sizeof(OUT) == 8 ? 53 : 24;  // mantissa bits
-    constexpr int BIAS = sizeof(OUT) == 8 ? 1023 : 127;
-    constexpr int EMAXB = sizeof(OUT) == 8 ? 2047 : 255;
-    bool neg = a.hi < 0;
-    unsigned long long hi = (unsigned long long)a.hi, lo = a.lo;
-    if (neg) {
-        lo = ~lo + 1ull;
-        hi = ~hi + (lo == 0 ? 1ull : 0ull);
-    }
-    if (hi == 0 && lo == 0) return (OUT)0;
-    int lz = hi ? __clzll(hi) : 64 + __clzll(lo);
-    if (lz >= 64) {
-        hi = lo << (lz - 64);
-        lo = 0;
-    } else if (lz > 0) {
-        hi = (hi << lz) | (lo >> (64 - lz));
-        lo <<= lz;
-    }
-    // leading bit at 127 of (hi:lo); keep P bits
-    unsigned long long m = hi >> (64 - P);
-    unsigned long long rest = hi << P;  // bits below the mantissa in hi, left-aligned
-    bool guard = (rest >> 63) & 1ull;
-    bool sticky = ((rest << 1) != 0) || lo != 0;
-    int e2 = (127 - lz) + scale;  // exponent of the leading bit
-    if (guard && (sticky || (m & 1ull))) {
-        ++m;
-        if (m >> P) {
-            m >>= 1;
-            ++e2;
-        }
-    }
-    int be = e2 + BIAS;
-    if (be <= 0) return neg ? -(OUT)0 : (OUT)0;  // below the normal range (not reached for sane x)
-    if (be >= EMAXB) return neg ? -(OUT)INFINITY : (OUT)INFINITY;
-    if (sizeof(OUT) == 8) {
-        unsigned long long bits =
-            ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
-        return (OUT)__longlong_as_double((long long)bits);
-    } else {
-        unsigned int bits = ((unsigned int)neg << 31) | ((unsigned int)be << 23) | (unsigned int)(m & ((1u << 23) - 1));
-        return (OUT)__int_as_float((int)bits);
-    }
 }
 
 // ------------------------------------------------------------------ mbarrier / bulk copy -----
@@ -510,7 +394,12 @@ __global__ void __launch_bounds__(kPT, 1)
     if (tid < kZeroPad * R) reinterpret_cast<XT*>(smem + kOwn + (tid / kZeroPad) * bstride)[cap - 1 + tid % kZeroPad] = 0;
     for (int q = tid; q < (1 << P.L1); q += kPT) t1[q] = (uint16_t)(__ldg(P.t1rank + q) * sizeof(XT));
     __syncthreads();
-    if (h->bad) {  // non-finite x: y is left unwritten and the error word is raised
+    if (h->bad) {  // an Inf or NaN in x: y is NaN and the error word is raised
+        for (uint32_t pi = blockIdx.x; pi < P.npanels; pi += gridDim.x) {
+            const uint64_t st = P.panel_start[pi];
+            const int C = (int)P.t1len[P.N - __popc(P.panel_s0[pi])];
+            for (int c = tid; c < C; c += kPT) y[st + c] = (OUT)NAN;
+        }
         if (blockIdx.x == 0 && tid == 0) atomicAdd(err, 1);
         return;
     }

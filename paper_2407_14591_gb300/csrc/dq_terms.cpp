@@ -13,6 +13,7 @@
 //
 // General Q (bosons): per-site digit functions f_i(n) from N and U, pair coefficients of
 // n_i n_j from NN, and a list of hops with the amplitude table sqrt((n_a + 1) n_b).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -119,6 +120,45 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         if (rc) return rc;
     }
     v.Cf = (float)v.C;
+    // Fixed-point coefficients for FP64 vectors: one exponent emin for all of them, chosen so
+    // that a row's diagonal (at most T_diag terms) stays below 2^62 in int64 and every hop
+    // coefficient below 2^57 (128-bit row sums). Relative to the largest coefficient the
+    // quantisation error is at most 2^-(Mbits+1).
+    {
+        double cmax = std::fabs(C);
+        for (int l = 0; l < nl; ++l) cmax = std::max(cmax, std::max(std::fabs(Kh[l]), std::fabs(Ah[l])));
+        for (double u : lin_host) cmax = std::max(cmax, std::fabs(u));
+        for (double u : pos) cmax = std::max(cmax, std::fabs(u));
+        int tdiag = 1 + (lin_host.empty() ? 0 : L);
+        for (int l = 0; l < nl; ++l) tdiag += __builtin_popcountll(v.dmask[l]);
+        int lg = 0;
+        while ((1 << lg) < tdiag) ++lg;
+        const int mbits = std::min(55, 62 - lg);
+        v.emin = cmax > 0.0 ? std::ilogb(cmax) + 1 - mbits : 0;
+        auto M = [&](double c) { return (long long)std::llrint(std::ldexp(c, -v.emin)); };
+        v.MC = M(C);
+        std::vector<long long> mka(2 * kMaxLayers, 0);
+        for (int l = 0; l < nl; ++l) {
+            mka[l] = M(Kh[l]);
+            mka[kMaxLayers + l] = M(Ah[l]);
+        }
+        int rc0;
+        void* q;
+        if ((rc0 = dev_upload(t->dev_allocs, mka.data(), mka.size() * 8, &q))) return rc0;
+        v.MKA = (const long long*)q;
+        if (!lin_host.empty()) {
+            std::vector<long long> ml(64, 0);
+            for (int p = 0; p < 64; ++p) ml[p] = M(lin_host[p]);
+            if ((rc0 = dev_upload(t->dev_allocs, ml.data(), ml.size() * 8, &q))) return rc0;
+            v.Mlin = (const long long*)q;
+        }
+        if (!pos.empty()) {
+            std::vector<long long> mp(pos.size());
+            for (size_t k = 0; k < pos.size(); ++k) mp[k] = M(pos[k]);
+            if ((rc0 = dev_upload(t->dev_allocs, mp.data(), mp.size() * 8, &q))) return rc0;
+            v.Mpos = (const long long*)q;
+        }
+    }
     std::vector<float> kaf(2 * kMaxLayers, 0.f);
     std::vector<double> ka(2 * kMaxLayers, 0.0);
     for (int l = 0; l < nl; ++l) {
