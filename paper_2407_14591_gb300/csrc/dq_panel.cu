@@ -467,15 +467,16 @@ __global__ void __launch_bounds__(kPT, 1)
         pc.ncls0 = (int)(hd & 255u);
         pc.np0 = pc.ncls0 + (int)((hd >> 8) & 255u);
         pc.nx = (int)((hd >> 16) & 255u);
-        const int ne = (pc.C + kPT - 1) / kPT;
-        if (ne > 4)
-            panel_rows<XT, OUT, NA, R, 7>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
-        else if (ne > 2)
-            panel_rows<XT, OUT, NA, R, 4>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
-        else if (ne == 2)
-            panel_rows<XT, OUT, NA, R, 2>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
-        else
-            panel_rows<XT, OUT, NA, R, 1>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
+        // rows per thread: the smallest E with E * kPT >= C (every E from 1 to 7 is compiled)
+        switch ((pc.C + kPT - 1) / kPT) {
+            case 7: panel_rows<XT, OUT, NA, R, 7>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+            case 6: panel_rows<XT, OUT, NA, R, 6>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+            case 5: panel_rows<XT, OUT, NA, R, 5>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+            case 4: panel_rows<XT, OUT, NA, R, 4>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+            case 3: panel_rows<XT, OUT, NA, R, 3>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+            case 2: panel_rows<XT, OUT, NA, R, 2>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+            default: panel_rows<XT, OUT, NA, R, 1>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
+        }
         __syncthreads();
     }
     if (fail) s_fail = 1;
