@@ -40,8 +40,8 @@ FALLBACK_HBM = 6800.0
 # kernel sources it was taken on; reported only while the sources are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the full-size product,
-    # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.25 GB read + 1.30 GB written
-    ("j1j2_square_6x5_N15", 2, "f64", 1, "deb0572598321000"): 19.55e9,
+    # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.24 GB read + 1.31 GB written
+    ("j1j2_square_6x5_N15", 2, "f64", 1, "b59fa4d5fb943da9"): 19.55e9,
 }
 
 WORKLOADS = {
