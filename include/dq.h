@@ -182,10 +182,16 @@ int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const void* x, void
  * T_q being term q with coefficient 1 (the operators of DQ_XY .. DQ_U). With a complex vector
  * stored as nrhs = 2 real columns this is Re <dy, T_q x>. The gradient with respect to x is
  * H dy (every term is real and Hermitian), i.e. another dq_matvec. x, dy: device arrays laid out
- * as in dq_matvec; d_grads: device array of n_terms doubles. Accumulation in FP64, reduced in a
- * fixed order (deterministic). Allocates and frees a small workspace; synchronous.
- * Errors as dq_make_terms, plus DQ_EINVAL for bad dtype or nrhs. The paper's operator class
- * (Sec. 4.1) has no derivatives; this serves training-style use of the product. */
+ * as in dq_matvec; d_grads: device array of n_terms doubles. For Q = 2 the products dy * x are
+ * exact fixed-point values (x and dy scaled per column to int64, each product rounded once to a
+ * common grid with 48 bits below the largest possible product) summed in int64; other Q multiply
+ * in FP64. Each block's sums are reduced in FP64 in a fixed order (deterministic). An Inf or NaN
+ * in x or dy (Q = 2) gives NaN gradients and raises the sector's error word. The workspace
+ * (2 * D * nrhs * 8 bytes for Q = 2, plus a few KB) is kept with the sector, grown on demand and
+ * freed by dq_free_sector; calls on one sector from several host threads at once race on it.
+ * Synchronous. Errors as dq_make_terms, plus DQ_EINVAL for bad dtype or nrhs, DQ_ENOMEM. The
+ * paper's operator class (Sec. 4.1) has no derivatives; this serves training-style use of the
+ * product. */
 int dq_term_grads(const dq_sector* s, const dq_term* terms, int n_terms, const void* x, const void* dy, int dtype,
                   int nrhs, double* d_grads, void* stream);
 

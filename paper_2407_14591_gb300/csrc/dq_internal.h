@@ -162,6 +162,8 @@ struct dq_sector {
     std::vector<void*> dev_allocs;
     int device;
     bool has_device;  // tables were uploaded (a CUDA device was present at creation)
+    void* grad_ws = nullptr;  // workspace of dq_term_grads, grown on demand, freed with the sector
+    size_t grad_ws_bytes = 0;
 };
 
 struct dq_terms {

@@ -396,6 +396,7 @@ int dq_make_sector(int L, int Q, int N, int n_sub, dq_sector** out) {
 
 void dq_free_sector(dq_sector* s) {
     if (!s) return;
+    if (s->grad_ws) cudaFree(s->grad_ws);
     free_dev(s->dev_allocs);
     delete s;
 }
