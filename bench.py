@@ -52,6 +52,7 @@ WORKLOADS = {
     "batched": 4,
     "diff": 5,
     "rank": 0,
+    "lanczos": 2,
 }
 
 
@@ -430,6 +431,34 @@ def run_rank(args, world, rank, local, dist, torch):
                   flush=True)
 
 
+def run_lanczos(args, world, rank, local, dist, torch):
+    """Workload 2's Lanczos form at full size: the same seeded start vector with FP64 vectors and
+    with FP32 vectors (FP64 alpha/beta recurrence and dot products in both), plain three-term
+    recurrence (full re-orthogonalisation would cost D*k FP64 operations per step here).
+    One JSON line: E0 of both, their relative difference, time per Lanczos step."""
+    from paper_2407_14591_gb300 import binding as b
+
+    steps = args.lanczos_steps
+    w, s, x_np = build_workload(2, args.n_sub, args.N)
+    t = b.make_terms(s, w.terms)
+    out = {}
+    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+        v0 = torch.from_numpy(x_np).to("cuda", dt)
+        b.lanczos(s, t, v0, 3, reorth=False)  # warm-up (scratch, tables)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = b.lanczos(s, t, v0, steps, reorth=False)
+        el = time.perf_counter() - t0
+        out[name] = {"E0": r["E0"], "steps_done": r["steps_done"], "ms_per_step": 1e3 * el / max(r["steps_done"], 1)}
+        del v0
+    rel = abs(out["f32"]["E0"] - out["f64"]["E0"]) / abs(out["f64"]["E0"])
+    if rank == 0:
+        print(json.dumps({"metric": "Lanczos E0, FP32 vectors vs FP64 vectors", "value": rel, "unit": "relative",
+                          "higher_is_better": False, "n_gpus": world, "steps": steps, "data": "synthetic",
+                          "config": {"workload": w.name, "D": s.dim, "n_sub": s.n_sub, "reorth": False},
+                          "f64": out["f64"], "f32": out["f32"]}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -444,6 +473,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the workload-1 Lanczos E0 check")
+    ap.add_argument("--lanczos-steps", type=int, default=40, help="steps of --workload lanczos")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -464,9 +494,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2407_14591_gb300 import binding as b
 
-    if args.workload in ("batched", "diff", "rank"):
-        {"batched": run_batched, "diff": run_diff, "rank": run_rank}[args.workload](args, world, rank, local, dist,
-                                                                                    torch)
+    if args.workload in ("batched", "diff", "rank", "lanczos"):
+        {"batched": run_batched, "diff": run_diff, "rank": run_rank,
+         "lanczos": run_lanczos}[args.workload](args, world, rank, local, dist, torch)
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
