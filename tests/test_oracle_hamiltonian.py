@@ -218,31 +218,33 @@ def test_planted_mistakes_are_caught(monkeypatch):
 
 def test_lanczos_golden_workload1_matches_sparse_eigensolver():
     """The stored oracle Lanczos E0 of workload 1 (L = 20 ring, N = 10) equals the smallest
-    eigenvalue of the Heisenberg Hamiltonian built from Kronecker products over the full 2^20
-    space and restricted to the N = 10 sector (ARPACK), independently of the oracle."""
+    eigenvalue (ARPACK) of the Heisenberg Hamiltonian written out independently of the oracle:
+    basis = all 20-bit words with ten set bits (any order), S+S- + S-S+ / 2 as pair flips located
+    through a dense word -> position table, SzSz = +-1/4 on the diagonal."""
     import scipy.sparse as sps
     from scipy.sparse.linalg import eigsh
 
     rows = dict((r[0], r[1:]) for r in read_golden("lanczos_workload1.txt"))
     E0 = float(rows["E0"][0])
     L = 20
-    sz = sps.csr_matrix(np.diag([0.5, -0.5]))
-    splus = sps.csr_matrix(np.array([[0.0, 1.0], [0.0, 0.0]]))
-    sminus = splus.T.tocsr()
-
-    def site_op(op, i):
-        return sps.kron(sps.kron(sps.identity(2 ** i, format="csr"), op, format="csr"),
-                        sps.identity(2 ** (L - 1 - i), format="csr"), format="csr")
-
-    Z = [site_op(sz, i) for i in range(L)]
-    P = [site_op(splus, i) for i in range(L)]
-    M = [site_op(sminus, i) for i in range(L)]
-    H = sps.csr_matrix((2 ** L, 2 ** L))
+    words = np.arange(1 << L, dtype=np.int64)
+    pop = np.zeros(1 << L, dtype=np.int64)
+    for b in range(L):
+        pop += (words >> b) & 1
+    states = words[pop == 10]
+    pos = np.full(1 << L, -1, dtype=np.int64)
+    pos[states] = np.arange(states.size)
+    diag = np.zeros(states.size)
+    r_idx, c_idx = [], []
     for i in range(L):
         j = (i + 1) % L
-        H = H + Z[i] @ Z[j] + 0.5 * (P[i] @ M[j] + M[i] @ P[j])
-    pop = np.array([bin(k).count("1") for k in range(2 ** L)])
-    idx = np.flatnonzero(pop == 10)
-    Hs = H[idx][:, idx]
-    ev = eigsh(Hs, k=1, which="SA", tol=1e-13)[0][0]
+        bi, bj = (states >> i) & 1, (states >> j) & 1
+        diag += np.where(bi == bj, 0.25, -0.25)
+        m = np.flatnonzero(bi != bj)
+        r_idx.append(m)
+        c_idx.append(pos[states[m] ^ ((1 << i) | (1 << j))])
+    r_idx, c_idx = np.concatenate(r_idx), np.concatenate(c_idx)
+    assert (c_idx >= 0).all()
+    H = sps.csr_matrix((np.full(r_idx.size, 0.5), (r_idx, c_idx)), shape=(states.size,) * 2) + sps.diags(diag)
+    ev = eigsh(H, k=1, which="SA", tol=1e-13)[0][0]
     assert abs(E0 - ev) <= 1e-9 * abs(ev)
