@@ -145,11 +145,12 @@ def subsystem_fields(words: np.ndarray, L: int, Q: int, part: list[int]):
 
 
 def composite_key(words: np.ndarray, L: int, Q: int, part: list[int]) -> np.ndarray:
-    """Pack the sort key (n_0, sigma^(0), ..., n_{K-1}, sigma^(K-1)) into one uint64.
+    """Pack the sort key (n_0, sigma^(0), ..., n_{K-1}, sigma^(K-1)) into one integer per word.
 
     Each n_k gets bit_length((Q-1) L_k) bits and each sigma^(k) Nbits L_k bits, most significant
-    field first, so integer order of the packed key is the tuple order. Raises if the key needs
-    more than 64 bits.
+    field first, so integer order of the packed key is the tuple order. The key is a uint64 when
+    it fits in 64 bits; otherwise (words of up to 64 bits plus the n_k fields) it is an array of
+    exact Python integers, which sort and binary-search the same way (small sectors only).
     """
     nb = nbits_for(Q)
     widths = []
@@ -157,7 +158,11 @@ def composite_key(words: np.ndarray, L: int, Q: int, part: list[int]) -> np.ndar
         widths.append(((Q - 1) * Lk).bit_length())
         widths.append(nb * Lk)
     if sum(widths) > 64:
-        raise ValueError("sort key does not fit in 64 bits for this partition")
+        key = np.zeros(words.shape, dtype=object)
+        for (n_k, sig), (wn, ws) in zip(subsystem_fields(words, L, Q, part), zip(widths[0::2], widths[1::2])):
+            key = (key << wn) | np.array([int(v) for v in n_k.ravel()], dtype=object).reshape(words.shape)
+            key = (key << ws) | np.array([int(v) for v in sig.ravel()], dtype=object).reshape(words.shape)
+        return key
     key = np.zeros(words.shape, dtype=np.uint64)
     for (n_k, sig), (wn, ws) in zip(subsystem_fields(words, L, Q, part), zip(widths[0::2], widths[1::2])):
         key = (key << np.uint64(wn)) | n_k.astype(np.uint64)

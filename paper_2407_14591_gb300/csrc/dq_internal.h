@@ -14,7 +14,7 @@ namespace dq {
 
 constexpr int kMaxSub = 64;      // at most one subsystem per site (L * Nbits <= 64)
 constexpr int kMaxTables = 2;    // most-equal partitions have at most two distinct lengths
-constexpr int kMaxLayers = 48;   // bond layers of the Q = 2 operator form
+constexpr int kMaxLayers = 64;   // bond layers of the Q = 2 operator form (>= the 63 distances of 64 sites)
 constexpr int kMaxTabBits = 24;  // widest subsystem pattern that gets a rank table
 
 // Plain-old-data view of a sector, passed by value to kernels. Device pointers only.

@@ -68,6 +68,23 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     // group by distance
     std::map<int, std::vector<std::pair<int, std::pair<double, double>>>> byd;
     for (auto& kv : pairs) byd[kv.first.second].push_back({kv.first.first, kv.second});
+    // A distance with at most three coefficient groups becomes one layer per group (uniform
+    // coefficients); otherwise one per-position layer. If the grouped form would need more than
+    // kMaxLayers layers, every distance with more than one group takes the per-position form, so
+    // at most one layer per distance (at most 63) remains.
+    int max_groups = 3;
+    {
+        int count = 0;
+        for (auto& kv : byd) {
+            std::map<std::pair<double, double>, int> g;
+            for (auto& e : kv.second) g[e.second] = 1;
+            int nz = 0;
+            for (auto& e : g)
+                if (e.first.first != 0.0 || e.first.second != 0.0) ++nz;
+            count += g.size() <= 3 ? nz : 1;
+        }
+        if (count > kMaxLayers) max_groups = 1;
+    }
     int nl = 0;
     int hops = 0;
     for (auto& kv : byd) {
@@ -77,7 +94,7 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         for (auto& e : lst) groups[e.second] |= 1ull << e.first;
         for (auto& e : lst)
             if (e.second.second != 0.0) ++hops;
-        if (groups.size() <= 3) {
+        if ((int)groups.size() <= max_groups) {
             for (auto& g : groups) {
                 if (g.first.first == 0.0 && g.first.second == 0.0) continue;
                 if (nl >= kMaxLayers) return set_error(DQ_EINVAL, "too many bond layers");

@@ -41,7 +41,8 @@ def test_library_exports_every_declared_symbol():
 
 
 CASES = [(9, 2, 4, 3), (10, 2, 5, 2), (12, 2, 6, 5), (11, 2, 4, 11), (8, 3, 7, 3), (7, 4, 9, 2), (9, 3, 5, 4),
-         (6, 5, 10, 3), (5, 16, 20, 2), (12, 2, 0, 3), (12, 2, 12, 2), (11, 4, 11, 2), (16, 2, 8, 1), (13, 3, 11, 0)]
+         (6, 5, 10, 3), (5, 16, 20, 2), (12, 2, 0, 3), (12, 2, 12, 2), (11, 4, 11, 2), (16, 2, 8, 1), (13, 3, 11, 0),
+         (64, 2, 2, 4), (64, 2, 3, 3), (32, 4, 3, 3)]
 
 
 @pytest.mark.parametrize("L,Q,N,n_sub", CASES)

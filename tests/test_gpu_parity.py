@@ -50,7 +50,8 @@ def gpu_matvec(sec, terms, x_np, dtype=torch.float64):
 # ---------------------------------------------------------------- rank / unrank -------------
 
 @pytest.mark.parametrize("L,Q,N,n_sub", [(20, 2, 10, 2), (14, 4, 14, 2), (24, 2, 12, 2), (12, 3, 9, 3),
-                                          (16, 2, 8, 16), (10, 5, 17, 4), (5, 16, 30, 2), (18, 2, 7, 1)])
+                                          (16, 2, 8, 16), (10, 5, 17, 4), (5, 16, 30, 2), (18, 2, 7, 1),
+                                          (64, 2, 2, 4), (64, 2, 3, 3), (32, 4, 3, 3)])
 def test_unrank_rank_whole_sector_bit_exact(L, Q, N, n_sub):
     s = b.make_sector(L, Q, N, n_sub)
     o = oracle_sector(L, Q, N, s.partition)
@@ -120,7 +121,8 @@ def random_terms(rng, L, Q, nbonds, disorder=True):
 
 
 SMALL = [(12, 2, 6, 2), (12, 2, 5, 3), (13, 2, 6, 13), (12, 2, 6, 1), (10, 3, 9, 2), (8, 4, 11, 3), (9, 3, 7, 9),
-         (7, 5, 12, 2), (6, 16, 30, 2), (16, 2, 8, 4), (11, 2, 0, 2), (11, 2, 11, 3), (5, 4, 15, 2), (14, 2, 1, 5)]
+         (7, 5, 12, 2), (6, 16, 30, 2), (16, 2, 8, 4), (11, 2, 0, 2), (11, 2, 11, 3), (5, 4, 15, 2), (14, 2, 1, 5),
+         (64, 2, 2, 4), (64, 2, 3, 3), (32, 4, 3, 3)]  # the last three: words of all 64 bits
 
 
 @pytest.mark.parametrize("L,Q,N,n_sub", SMALL)

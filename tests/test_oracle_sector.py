@@ -267,3 +267,30 @@ def test_composite_key_is_tuple_order():
     tuples = [tuple(v for n, s in fields for v in (int(n[r]), int(s[r]))) for r in range(len(words))]
     assert np.argsort(keys, kind="stable").tolist() == sorted(range(len(words)), key=lambda r: tuples[r])
     assert np.array_equal(sec.basis, words[np.argsort(keys, kind="stable")])
+
+
+@pytest.mark.parametrize("L,Q,N,part", [(64, 2, 2, [16, 16, 16, 16]), (64, 2, 3, [32, 32]), (32, 4, 3, [11, 11, 10])])
+def test_full_width_words_sort_by_the_key_tuple(L, Q, N, part):
+    """Sectors whose words use all 64 bits (the sort key then needs more than 64 bits): the
+    canonical order equals Python's sort of the words by the tuple (n_0, sigma^(0), n_1, ...)
+    built digit by digit, and rank(unrank(i)) = i."""
+    o = OracleSector(L, Q, N, partition=part)
+    nb = (Q - 1).bit_length()
+
+    def digits(w):
+        return [(w >> (nb * (L - 1 - i))) & ((1 << nb) - 1) for i in range(L)]
+
+    def key(w):
+        d, out, s = digits(w), [], 0
+        for Lk in part:
+            sub = d[s:s + Lk]
+            out.append(sum(sub))
+            out.append(tuple(sub))
+            s += Lk
+        return tuple(out)
+
+    words = sorted((int(w) for w in o.basis), key=key)
+    assert [int(w) for w in o.basis] == words
+    assert all(sum(digits(w)) == N for w in words[:50])
+    idx = np.arange(0, o.dim, max(1, o.dim // 500))
+    assert np.array_equal(o.index_of_many(o.basis[idx]), idx)
