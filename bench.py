@@ -474,6 +474,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the workload-1 Lanczos E0 check")
     ap.add_argument("--lanczos-steps", type=int, default=40, help="steps of --workload lanczos")
+    ap.add_argument("--graph", type=int, default=0,
+                    help="also time this many products captured in one CUDA graph (launch-free rate)")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -537,6 +539,29 @@ def main():
         barrier()
     kern_ms, kern_calls, kernels = b.timing_read()
     b.timing_enable(False)
+
+    graph = None
+    if args.graph:
+        # launch-free rate: args.graph products captured once in a CUDA graph, replayed
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            for _ in range(args.graph):
+                b.matvec(s, t, x, y)
+        for _ in range(2):
+            g.replay()
+        torch.cuda.synchronize()
+        reps = 5
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / (reps * args.graph)
+        graph = {"products_per_graph": args.graph, "replays": reps, "ms_per_product": gms,
+                 "elements_per_s": world * s.dim * args.nrhs / (gms / 1e3)}
+        del g
+
     def red(op):
         def f(v):
             if dist is None:
@@ -610,6 +635,7 @@ def main():
             "e2e": e2e,
             "cpu_baseline": cpu,
             "lanczos": lz,
+            "graph": graph,
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

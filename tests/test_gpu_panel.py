@@ -143,3 +143,30 @@ def test_timing_hooks_count_and_time_the_main_kernel():
     assert ms > 0.0
     b.matvec(s, tp, x)  # timing off: nothing more is recorded
     assert b.timing_read()[1] == 4
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_products_replay_from_a_cuda_graph(dtype):
+    """dq_matvec captured in a CUDA graph (after one eager call has set up its scratch) gives,
+    on replay with new x, exactly what an eager call gives: panel path and general path."""
+    rng = np.random.default_rng(12)
+    cases = [(b.make_sector(20, 2, 10, 2), wl.heisenberg_terms(wl.chain_bonds(20), 1.0, 1.0), "panel"),
+             (b.make_sector(14, 2, 7, 3), wl.heisenberg_terms(wl.chain_bonds(14), rng.uniform(0.5, 1.5, 14), 1.0)
+              + wl.field_terms(rng.uniform(-3, 3, 14)), "general")]
+    for s, terms, path in cases:
+        t = b.make_terms(s, terms)
+        assert t.path == path
+        x = torch.rand(s.dim, dtype=dtype, device=DEV)
+        y = torch.empty_like(x)
+        b.matvec(s, t, x, y)  # first call: scratch
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="relaxed"):
+            b.matvec(s, t, x, y)
+        for _ in range(2):
+            x.copy_(torch.rand(s.dim, dtype=dtype, device=DEV) - 0.5)
+            g.replay()
+            torch.cuda.synchronize()
+            ref = b.matvec(s, t, x)
+            assert torch.equal(y, ref)
+        s.check_device()
