@@ -89,6 +89,12 @@ struct DevTermsQG {
     const float* pair_Kf;
     const float* hop_tf;
     const float* ampf;
+    // Fixed-point copies used when the vectors are FP64: c = M 2^emin
+    int emin;
+    long long MC;
+    const long long* Msite;  // [nsite][Q]
+    const long long* Mpair;  // [npair]
+    const long long* Mhop;   // [nhop][Q][Q]: -t sqrt((n_a + 1) n_b), zero where the hop is not allowed
 };
 
 // Plan of the panel product (Q = 2, two subsystems, Sec. 3.3): with index = c_0(s0) + index_1(s1),

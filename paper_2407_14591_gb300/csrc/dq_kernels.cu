@@ -63,42 +63,21 @@ __device__ __forceinline__ T cf(double d, float f) {
         return f;
 }
 
-// y = H x, Q = 2 operator in bond-layer form. LIN2 selects the two-table rank.
+// y = H x, Q = 2 operator in bond-layer form, FP32 vectors (FP32 coefficient copies, compensated
+// FP32 sums; FP64 vectors take k_matvec_q2_fx). LIN2 selects the two-table rank.
 template <typename T, bool LIN2>
 __global__ void __launch_bounds__(256) k_matvec_q2(DevSector S, DevTermsQ2 H, const T* __restrict__ x,
                                                    T* __restrict__ y, int ld, int col0, int ch, bool use_sm) {
+    static_assert(sizeof(T) == 4, "FP32 vectors only");
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
-    const T* posT = sizeof(T) == 8 ? (const T*)H.pos : (const T*)H.posf;
+    const T* posT = H.posf;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = d_unrank(S, off_s, str_s, i);
-        // diagonal: FP64 vectors in FP64; FP32 vectors with FP32 coefficients, compensated
+        // diagonal with FP32 coefficients, compensated
         T dv;
-        if constexpr (sizeof(T) == 8) {
-            double d = H.C;
-            if (H.lin) {
-                uint64_t m = s;
-                while (m) {
-                    int p = __ffsll((long long)m) - 1;
-                    m &= m - 1;
-                    d += H.lin[p];
-                }
-            }
-            for (int l = 0; l < H.nl; ++l) {
-                uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
-                if (H.kpos[l] < 0) {
-                    d += __ldg(H.KA + l) * (double)__popcll(a);
-                } else {
-                    while (a) {
-                        int p = __ffsll((long long)a) - 1;
-                        a &= a - 1;
-                        d += H.pos[H.kpos[l] + p];
-                    }
-                }
-            }
-            dv = d;
-        } else {
+        {
             RowAcc<float> d;
             d.init(H.Cf);
             if (H.linf) {
@@ -173,19 +152,82 @@ __global__ void __launch_bounds__(256)
         row_q2_fx<CH, LIN2>(S, H, off_s, str_s, i, X, ld, col0, ch, sc, y);
 }
 
-// y = H x, general-Q operator (bosons).
+// y = H x, general-Q operator (bosons), FP64 vectors in exact fixed point: digit functions and
+// n_i n_j pairs summed in int64, every allowed hop b+_a b_b a 128-bit multiply-add of its
+// amplitude -t sqrt((n_a + 1) n_b) (an integer on the grid 2^emin) with the gathered X.
+template <bool LIN2, int CH>
+__global__ void __launch_bounds__(256)
+    k_matvec_qg_fx(DevSector S, DevTermsQG H, const long long* __restrict__ X, double* __restrict__ y,
+                   const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    if (hdr->bad) {  // an Inf or NaN in x: y is NaN and the error word is raised
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
+            for (int c = 0; c < ch; ++c) y[i * ld + col0 + c] = __longlong_as_double(0x7ff8000000000000ll);
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(S.err, 1);
+        return;
+    }
+    int sc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin - hdr->F[col0 + c] : 0;
+    const int Q = S.Q;
+    const uint64_t dm = (1ull << S.nb) - 1;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step) {
+        const uint64_t s = d_unrank(S, off_s, str_s, i);
+        long long md = H.MC;
+        for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite + q * Q + (int)((s >> H.site_sh[q]) & dm));
+        for (int q = 0; q < H.npair; ++q) {
+            const int a = (int)((s >> H.pair_sh[2 * q]) & dm), b = (int)((s >> H.pair_sh[2 * q + 1]) & dm);
+            md += __ldg(H.Mpair + q) * (long long)(a * b);
+        }
+        I128 r[CH];
+        const long long* Xi = X + i * ld + col0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            r[c] = {0, 0};
+            if (c < ch) mac(r[c], md, __ldg(Xi + c));
+        }
+        for (int q = 0; q < H.nhop; ++q) {
+            const int sa = H.hop_sh[2 * q], sb = H.hop_sh[2 * q + 1];
+#pragma unroll
+            for (int dir = 0; dir < 2; ++dir) {
+                const int s_up = dir ? sb : sa, s_dn = dir ? sa : sb;  // b+_up b_dn
+                const int nu = (int)((s >> s_up) & dm), nd = (int)((s >> s_dn) & dm);
+                if (nu < Q - 1 && nd > 0) {
+                    const uint64_t s2 = s + (1ull << s_up) - (1ull << s_dn);
+                    const uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
+                    const long long M = __ldg(H.Mhop + ((size_t)q * Q + nu) * Q + nd);
+                    const long long* Xj = X + j * ld + col0;
+#pragma unroll
+                    for (int c = 0; c < CH; ++c)
+                        if (c < ch) mac(r[c], M, __ldg(Xj + c));
+                }
+            }
+        }
+        double* yi = y + i * ld + col0;
+#pragma unroll
+        for (int c = 0; c < CH; ++c)
+            if (c < ch) yi[c] = i128_to<double>(r[c], sc[c]);
+    }
+}
+
+// y = H x, general-Q operator (bosons), FP32 vectors (FP32 coefficient copies, compensated FP32
+// sums; FP64 vectors take k_matvec_qg_fx).
 template <typename T, bool LIN2>
 __global__ void __launch_bounds__(256) k_matvec_qg(DevSector S, DevTermsQG H, const T* __restrict__ x,
                                                    T* __restrict__ y, int ld, int col0, int ch, bool use_sm) {
+    static_assert(sizeof(T) == 4, "FP32 vectors only");
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
     const int Q = S.Q;
     const uint64_t dm = (1ull << S.nb) - 1;
-    const T* siteT = sizeof(T) == 8 ? (const T*)H.site_f : (const T*)H.site_ff;
-    const T* pairT = sizeof(T) == 8 ? (const T*)H.pair_K : (const T*)H.pair_Kf;
-    const T* hopT = sizeof(T) == 8 ? (const T*)H.hop_t : (const T*)H.hop_tf;
-    const T* ampT = sizeof(T) == 8 ? (const T*)H.amp : (const T*)H.ampf;
+    const T* siteT = H.site_ff;
+    const T* pairT = H.pair_Kf;
+    const T* hopT = H.hop_tf;
+    const T* ampT = H.ampf;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
         const uint64_t s = d_unrank(S, off_s, str_s, i);
         RowAcc<T> d;
@@ -286,10 +328,9 @@ static int launch_matvec_t(const dq_sector* s, const dq_terms* t, const T* x, T*
     return (int)cudaGetLastError();
 }
 
-// FP64 vectors with the Q = 2 operator: column prepass into the terms' scratch, then the
-// fixed-point kernel.
-static int launch_matvec_q2_fx(const dq_sector* s, dq_terms* t, const double* x, double* y, int nrhs,
-                               cudaStream_t st) {
+// FP64 vectors: column prepass into the terms' scratch, then the fixed-point kernel of the
+// operator's form (Q = 2 bond layers or general Q).
+static int launch_matvec_fx(const dq_sector* s, dq_terms* t, const double* x, double* y, int nrhs, cudaStream_t st) {
     const size_t need = kColScaleBytes + (size_t)s->D * nrhs * sizeof(long long);
     if (t->scratch_bytes < need) {
         if (t->scratch) cudaFree(t->scratch);
@@ -311,16 +352,30 @@ static int launch_matvec_q2_fx(const dq_sector* s, dq_terms* t, const double* x,
     int passes = 0;
     for (int c0 = 0; c0 < nrhs; c0 += kMaxCh, ++passes) {
         const int ch = nrhs - c0 < kMaxCh ? nrhs - c0 : kMaxCh;
-        if (nrhs == 1) {
-            if (lin2)
-                k_matvec_q2_fx<true, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
-            else
-                k_matvec_q2_fx<false, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+        if (t->q2) {
+            if (nrhs == 1) {
+                if (lin2)
+                    k_matvec_q2_fx<true, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+                else
+                    k_matvec_q2_fx<false, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            } else {
+                if (lin2)
+                    k_matvec_q2_fx<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+                else
+                    k_matvec_q2_fx<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            }
         } else {
-            if (lin2)
-                k_matvec_q2_fx<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
-            else
-                k_matvec_q2_fx<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            if (nrhs == 1) {
+                if (lin2)
+                    k_matvec_qg_fx<true, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                else
+                    k_matvec_qg_fx<false, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            } else {
+                if (lin2)
+                    k_matvec_qg_fx<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                else
+                    k_matvec_qg_fx<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            }
         }
     }
     timing_stop(tslot, st, 2 + passes);
@@ -330,9 +385,7 @@ static int launch_matvec_q2_fx(const dq_sector* s, dq_terms* t, const double* x,
 int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (t->panel_ok && nrhs == 1) return launch_panel_matvec(s, const_cast<dq_terms*>(t), x, y, dtype, stream);
-    if (dtype == DQ_F64 && t->q2)
-        return launch_matvec_q2_fx(s, const_cast<dq_terms*>(t), (const double*)x, (double*)y, nrhs, st);
-    if (dtype == DQ_F64) return launch_matvec_t<double>(s, t, (const double*)x, (double*)y, nrhs, st);
+    if (dtype == DQ_F64) return launch_matvec_fx(s, const_cast<dq_terms*>(t), (const double*)x, (double*)y, nrhs, st);
     return launch_matvec_t<float>(s, t, (const float*)x, (float*)y, nrhs, st);
 }
 

@@ -287,6 +287,37 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     if ((rc = upf(pair_K, &v.pair_Kf))) return rc;
     if ((rc = upf(hop_t, &v.hop_tf))) return rc;
     if ((rc = upf(amp, &v.ampf))) return rc;
+    // Fixed-point coefficients for FP64 vectors, as for Q = 2 (compile_q2): one exponent emin,
+    // a row's diagonal (at most T_diag unit terms, a pair counting (Q-1)^2) below 2^62 in int64,
+    // every hop amplitude below 2^55.
+    {
+        std::vector<double> hop_amp((size_t)v.nhop * Q * Q, 0.0);
+        for (int q = 0; q < v.nhop; ++q)
+            for (int a = 0; a < Q - 1; ++a)
+                for (int b = 1; b < Q; ++b) hop_amp[((size_t)q * Q + a) * Q + b] = -hop_t[q] * amp[(size_t)a * Q + b];
+        double cmax = 0.0;
+        for (double u : site_f) cmax = std::max(cmax, std::fabs(u));
+        for (double u : pair_K) cmax = std::max(cmax, std::fabs(u));
+        for (double u : hop_amp) cmax = std::max(cmax, std::fabs(u));
+        const long long tdiag = 1 + (long long)v.nsite + (long long)v.npair * (Q - 1) * (Q - 1);
+        int lg = 0;
+        while ((1ll << lg) < tdiag) ++lg;
+        const int mbits = std::min(55, 62 - lg);
+        v.emin = cmax > 0.0 ? std::ilogb(cmax) + 1 - mbits : 0;
+        auto M = [&](double c) { return (long long)std::llrint(std::ldexp(c, -v.emin)); };
+        v.MC = 0;
+        auto upm = [&](const std::vector<double>& src, const long long** dst) -> int {
+            std::vector<long long> m(src.size());
+            for (size_t k = 0; k < src.size(); ++k) m[k] = M(src[k]);
+            void* q;
+            int r = dev_upload(t->dev_allocs, m.data(), m.size() * 8, &q);
+            *dst = (const long long*)q;
+            return r;
+        };
+        if ((rc = upm(site_f, &v.Msite))) return rc;
+        if ((rc = upm(pair_K, &v.Mpair))) return rc;
+        if ((rc = upm(hop_amp, &v.Mhop))) return rc;
+    }
     return DQ_OK;
 }
 
