@@ -149,10 +149,11 @@ void dq_free_terms(dq_terms* t);
  * FP64 vectors are summed exactly in fixed point: each column of x is scaled by a power of two
  * and rounded to a 57-bit integer, the coefficients share one power-of-two grid (at least 55
  * significant bits relative to the largest, fewer by log2 of a row's diagonal term count when
- * that exceeds 128), and each y[i] is a 128-bit integer sum rounded once. An Inf or NaN in FP64 x
- * makes y NaN and raises the sector's error word (DQ_EDEVICE from dq_check_device). FP32 vectors
- * use FP32 coefficient copies and compensated FP32 sums. The call keeps a scratch area of
- * D * nrhs * 8 bytes with the terms (allocated on first use).
+ * that exceeds 128), and each y[i] is a 128-bit integer sum rounded once. FP32 vectors take the
+ * same route with 31-bit integers for x, hop amplitudes with 24 significant bits (int64 hop
+ * sums) and the diagonal on a finer grid. An Inf or NaN in x makes y NaN and raises the sector's
+ * error word (DQ_EDEVICE from dq_check_device). The call keeps a scratch area of
+ * D * nrhs * 8 bytes (FP64) or 4 bytes (FP32) with the terms, allocated on first use.
  * Errors: DQ_EINVAL (NULL pointers, bad dtype or nrhs, terms of another sector). */
 int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
 

@@ -67,34 +67,38 @@ struct DevTermsQ2 {
     const long long* MKA;
     const long long* Mlin;  // NULL when lin is
     const long long* Mpos;
+    // Fixed-point copies used when the vectors are FP32: hop amplitudes c = m 2^emin32 with
+    // |m| < 2^24 (int32); diagonal coefficients on their own finer grid c = m 2^emin32d (int64),
+    // 0 <= emin32 - emin32d <= 60
+    int emin32, emin32d;
+    long long MC32;
+    const long long* MKA32;  // K of layer l (grid emin32d) at l, A (grid emin32) at kMaxLayers + l
+    const long long* Mlin32;
+    const long long* Mpos32;  // per-position K (grid emin32d) and A (grid emin32) values
 };
 static_assert(sizeof(DevSector) + sizeof(DevTermsQ2) + 64 <= 4096, "product kernel parameters exceed 4 KB");
 
 // General-Q operator (bosons): per-site digit functions, density-density pairs, hops.
 struct DevTermsQG {
-    double C;
-    int nsite;           // sites with a nonzero digit function
+    int nsite;           // sites with a nonzero digit function f_i(d)
     const int* site_sh;  // bit shift of each such site's digit
-    const double* site_f;  // [nsite][Q] values f_i(d)
     int npair;
-    const int* pair_sh;    // [npair][2] shifts
-    const double* pair_K;  // coefficient of d_i d_j
+    const int* pair_sh;  // [npair][2] shifts of the n_i n_j pairs
     int nhop;
-    const int* hop_sh;     // [nhop][2] shifts (a, b): term -t (b+_a b_b + b+_b b_a)
-    const double* hop_t;
-    const double* amp;     // [Q][Q]: sqrt((n_a + 1) n_b)
-    // FP32 copies of the coefficients, used when the vectors are FP32
-    float Cf;
-    const float* site_ff;
-    const float* pair_Kf;
-    const float* hop_tf;
-    const float* ampf;
-    // Fixed-point copies used when the vectors are FP64: c = M 2^emin
+    const int* hop_sh;   // [nhop][2] shifts (a, b): term -t (b+_a b_b + b+_b b_a)
+    // Coefficients as integers on one grid, for FP64 vectors: c = M 2^emin
     int emin;
     long long MC;
-    const long long* Msite;  // [nsite][Q]
-    const long long* Mpair;  // [npair]
+    const long long* Msite;  // [nsite][Q]: f_i(d)
+    const long long* Mpair;  // [npair]: coefficient of d_i d_j
     const long long* Mhop;   // [nhop][Q][Q]: -t sqrt((n_a + 1) n_b), zero where the hop is not allowed
+    // The same for FP32 vectors: hop amplitudes m 2^emin32 with |m| < 2^24 (int32), diagonal
+    // coefficients on their own finer grid 2^emin32d (int64), 0 <= emin32 - emin32d <= 60
+    int emin32, emin32d;
+    long long MC32;
+    const long long* Msite32;
+    const long long* Mpair32;
+    const int* Mhop32;
 };
 
 // Plan of the panel product (Q = 2, two subsystems, Sec. 3.3): with index = c_0(s0) + index_1(s1),

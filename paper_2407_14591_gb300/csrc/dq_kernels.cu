@@ -54,81 +54,6 @@ __global__ void k_index_of(DevSector S, const uint64_t* __restrict__ in, uint64_
 
 constexpr int kMaxCh = 8;  // right-hand sides handled per pass
 
-// Coefficient in the vectors' precision (FP64 vectors: the FP64 value; FP32: its FP32 copy).
-template <typename T>
-__device__ __forceinline__ T cf(double d, float f) {
-    if constexpr (sizeof(T) == 8)
-        return d;
-    else
-        return f;
-}
-
-// y = H x, Q = 2 operator in bond-layer form, FP32 vectors (FP32 coefficient copies, compensated
-// FP32 sums; FP64 vectors take k_matvec_q2_fx). LIN2 selects the two-table rank.
-template <typename T, bool LIN2>
-__global__ void __launch_bounds__(256) k_matvec_q2(DevSector S, DevTermsQ2 H, const T* __restrict__ x,
-                                                   T* __restrict__ y, int ld, int col0, int ch, bool use_sm) {
-    static_assert(sizeof(T) == 4, "FP32 vectors only");
-    extern __shared__ uint64_t sm[];
-    const uint64_t *off_s, *str_s;
-    stage_os(S, sm, use_sm, off_s, str_s);
-    const T* posT = H.posf;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint64_t s = d_unrank(S, off_s, str_s, i);
-        // diagonal with FP32 coefficients, compensated
-        T dv;
-        {
-            RowAcc<float> d;
-            d.init(H.Cf);
-            if (H.linf) {
-                uint64_t m = s;
-                while (m) {
-                    int p = __ffsll((long long)m) - 1;
-                    m &= m - 1;
-                    d.add(H.linf[p]);
-                }
-            }
-            for (int l = 0; l < H.nl; ++l) {
-                uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
-                if (H.kpos[l] < 0) {
-                    if (a) d.add(__ldg(H.KAf + l) * (float)__popcll(a));
-                } else {
-                    while (a) {
-                        int p = __ffsll((long long)a) - 1;
-                        a &= a - 1;
-                        d.add(H.posf[H.kpos[l] + p]);
-                    }
-                }
-            }
-            dv = d.get();
-        }
-        RowAcc<T> acc[kMaxCh];
-        const T* xi = x + i * ld + col0;
-#pragma unroll
-        for (int c = 0; c < kMaxCh; ++c) acc[c].init(c < ch ? dv * __ldg(xi + c) : (T)0);
-        for (int l = 0; l < H.nl; ++l) {
-            uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
-            const uint64_t pm = 1ull | (1ull << H.dist[l]);
-            const T au = cf<T>(__ldg(H.KA + kMaxLayers + l), __ldg(H.KAf + kMaxLayers + l));
-            while (o) {
-                int p = __ffsll((long long)o) - 1;
-                o &= o - 1;
-                uint64_t s2 = s ^ (pm << p);
-                uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
-                const T amp = H.apos[l] < 0 ? au : posT[H.apos[l] + p];
-                const T* xj = x + j * ld + col0;
-#pragma unroll
-                for (int c = 0; c < kMaxCh; ++c)
-                    if (c < ch) acc[c].add(amp * __ldg(xj + c));
-            }
-        }
-        T* yi = y + i * ld + col0;
-#pragma unroll
-        for (int c = 0; c < kMaxCh; ++c)
-            if (c < ch) yi[c] = acc[c].get();
-    }
-}
-
 // y = H x, Q = 2 operator, FP64 vectors in exact fixed point (row_q2_fx). CH: right-hand
 // sides per pass (1, or kMaxCh for nrhs > 1).
 template <bool LIN2, int CH>
@@ -213,60 +138,87 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// y = H x, general-Q operator (bosons), FP32 vectors (FP32 coefficient copies, compensated FP32
-// sums; FP64 vectors take k_matvec_qg_fx).
-template <typename T, bool LIN2>
-__global__ void __launch_bounds__(256) k_matvec_qg(DevSector S, DevTermsQG H, const T* __restrict__ x,
-                                                   T* __restrict__ y, int ld, int col0, int ch, bool use_sm) {
-    static_assert(sizeof(T) == 4, "FP32 vectors only");
+// y = H x for FP32 vectors in fixed point (int32 X, int32 hop amplitudes, int64 hop sums, the
+// diagonal on a finer int64 grid, one 128-bit combination and rounding per row): the Q = 2 form
+// (row_q2_f32x) and the general-Q form.
+template <bool LIN2, int CH>
+__global__ void __launch_bounds__(256)
+    k_matvec_q2_f32x(DevSector S, DevTermsQ2 H, const int* __restrict__ X, float* __restrict__ y,
+                     const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    if (hdr->bad) {  // an Inf or NaN in x: y is NaN and the error word is raised
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
+            for (int c = 0; c < ch; ++c) y[i * ld + col0 + c] = __int_as_float(0x7fc00000);
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(S.err, 1);
+        return;
+    }
+    int sc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin32d - hdr->F[col0 + c] : 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
+        row_q2_f32x<CH, LIN2>(S, H, off_s, str_s, i, X, ld, col0, ch, sc, y);
+}
+
+template <bool LIN2, int CH>
+__global__ void __launch_bounds__(256)
+    k_matvec_qg_f32x(DevSector S, DevTermsQG H, const int* __restrict__ X, float* __restrict__ y,
+                     const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    if (hdr->bad) {
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
+            for (int c = 0; c < ch; ++c) y[i * ld + col0 + c] = __int_as_float(0x7fc00000);
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(S.err, 1);
+        return;
+    }
+    int sc[CH];
+#pragma unroll
+    for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin32d - hdr->F[col0 + c] : 0;
     const int Q = S.Q;
     const uint64_t dm = (1ull << S.nb) - 1;
-    const T* siteT = H.site_ff;
-    const T* pairT = H.pair_Kf;
-    const T* hopT = H.hop_tf;
-    const T* ampT = H.ampf;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step) {
         const uint64_t s = d_unrank(S, off_s, str_s, i);
-        RowAcc<T> d;
-        d.init(cf<T>(H.C, H.Cf));
-        for (int q = 0; q < H.nsite; ++q) {
-            int n = (int)((s >> H.site_sh[q]) & dm);
-            d.add(siteT[q * Q + n]);
-        }
+        long long md = H.MC32;
+        for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite32 + q * Q + (int)((s >> H.site_sh[q]) & dm));
         for (int q = 0; q < H.npair; ++q) {
-            int a = (int)((s >> H.pair_sh[2 * q]) & dm), b = (int)((s >> H.pair_sh[2 * q + 1]) & dm);
-            if (a * b) d.add(pairT[q] * (T)(a * b));
+            const int a = (int)((s >> H.pair_sh[2 * q]) & dm), b = (int)((s >> H.pair_sh[2 * q + 1]) & dm);
+            md += __ldg(H.Mpair32 + q) * (long long)(a * b);
         }
-        const T dv = d.get();
-        RowAcc<T> acc[kMaxCh];
-        const T* xi = x + i * ld + col0;
+        long long hs[CH];
 #pragma unroll
-        for (int c = 0; c < kMaxCh; ++c) acc[c].init(c < ch ? dv * __ldg(xi + c) : (T)0);
+        for (int c = 0; c < CH; ++c) hs[c] = 0;
         for (int q = 0; q < H.nhop; ++q) {
             const int sa = H.hop_sh[2 * q], sb = H.hop_sh[2 * q + 1];
-            const T t = hopT[q];
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
                 const int s_up = dir ? sb : sa, s_dn = dir ? sa : sb;  // b+_up b_dn
-                int nu = (int)((s >> s_up) & dm), nd = (int)((s >> s_dn) & dm);
+                const int nu = (int)((s >> s_up) & dm), nd = (int)((s >> s_dn) & dm);
                 if (nu < Q - 1 && nd > 0) {
-                    uint64_t s2 = s + (1ull << s_up) - (1ull << s_dn);
-                    uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
-                    const T amp = -t * ampT[nu * Q + nd];
-                    const T* xj = x + j * ld + col0;
+                    const uint64_t s2 = s + (1ull << s_up) - (1ull << s_dn);
+                    const uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
+                    const long long M = __ldg(H.Mhop32 + ((size_t)q * Q + nu) * Q + nd);
+                    const int* Xj = X + j * ld + col0;
 #pragma unroll
-                    for (int c = 0; c < kMaxCh; ++c)
-                        if (c < ch) acc[c].add(amp * __ldg(xj + c));
+                    for (int c = 0; c < CH; ++c)
+                        if (c < ch) hs[c] += M * __ldg(Xj + c);
                 }
             }
         }
-        T* yi = y + i * ld + col0;
+        const int* Xi = X + i * ld + col0;
+        float* yi = y + i * ld + col0;
 #pragma unroll
-        for (int c = 0; c < kMaxCh; ++c)
-            if (c < ch) yi[c] = acc[c].get();
+        for (int c = 0; c < CH; ++c) {
+            if (c >= ch) continue;
+            I128 r = {0, 0};
+            mac(r, md, __ldg(Xi + c));
+            add_i64_shl(r, hs[c], H.emin32 - H.emin32d);
+            yi[c] = i128_to<float>(r, sc[c]);
+        }
     }
 }
 
@@ -299,32 +251,6 @@ int launch_state_at_batch(const DevSector& S, const uint64_t* d_index, uint64_t*
 int launch_index_of_batch(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream) {
     bool sm = os_in_smem(S);
     k_index_of<<<grid_for(n, 256, 8), 256, sm ? os_bytes(S) : 0, (cudaStream_t)stream>>>(S, d_state, d_index, n, sm);
-    return (int)cudaGetLastError();
-}
-
-template <typename T>
-static int launch_matvec_t(const dq_sector* s, const dq_terms* t, const T* x, T* y, int nrhs, cudaStream_t st) {
-    const DevSector& S = s->dev;
-    bool sm = os_in_smem(S);
-    size_t smb = sm ? os_bytes(S) : 0;
-    bool lin2 = (S.n_sub == 2);
-    unsigned grid = grid_for(S.D, 256, 8);
-    const int tslot = timing_start(st);
-    for (int c0 = 0; c0 < nrhs; c0 += kMaxCh) {
-        int ch = nrhs - c0 < kMaxCh ? nrhs - c0 : kMaxCh;
-        if (t->q2) {
-            if (lin2)
-                k_matvec_q2<T, true><<<grid, 256, smb, st>>>(S, t->q2v, x, y, nrhs, c0, ch, sm);
-            else
-                k_matvec_q2<T, false><<<grid, 256, smb, st>>>(S, t->q2v, x, y, nrhs, c0, ch, sm);
-        } else {
-            if (lin2)
-                k_matvec_qg<T, true><<<grid, 256, smb, st>>>(S, t->qgv, x, y, nrhs, c0, ch, sm);
-            else
-                k_matvec_qg<T, false><<<grid, 256, smb, st>>>(S, t->qgv, x, y, nrhs, c0, ch, sm);
-        }
-    }
-    timing_stop(tslot, st, (nrhs + kMaxCh - 1) / kMaxCh);
     return (int)cudaGetLastError();
 }
 
@@ -382,11 +308,51 @@ static int launch_matvec_fx(const dq_sector* s, dq_terms* t, const double* x, do
     return (int)cudaGetLastError();
 }
 
+// FP32 vectors: column prepass to int32 into the terms' scratch, then the FP32 fixed-point kernel.
+static int launch_matvec_f32x(const dq_sector* s, dq_terms* t, const float* x, float* y, int nrhs, cudaStream_t st) {
+    const size_t need = kColScaleBytes + (size_t)s->D * nrhs * sizeof(int);
+    if (t->scratch_bytes < need) {
+        if (t->scratch) cudaFree(t->scratch);
+        t->scratch = nullptr;
+        t->scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&t->scratch, need);
+        if (e != cudaSuccess) return (int)e;
+        t->scratch_bytes = need;
+    }
+    ColScale* h = reinterpret_cast<ColScale*>(t->scratch);
+    int* X = reinterpret_cast<int*>(reinterpret_cast<char*>(t->scratch) + kColScaleBytes);
+    launch_col_prepass<float, int>(x, X, s->D, nrhs, h, num_sms(), st);
+    const DevSector& S = s->dev;
+    const bool sm = os_in_smem(S);
+    const size_t smb = sm ? os_bytes(S) : 0;
+    const bool lin2 = (S.n_sub == 2);
+    const unsigned grid = grid_for(S.D, 256, 8);
+    const int tslot = timing_start(st);
+    int passes = 0;
+    for (int c0 = 0; c0 < nrhs; c0 += kMaxCh, ++passes) {
+        const int ch = nrhs - c0 < kMaxCh ? nrhs - c0 : kMaxCh;
+        const bool one = nrhs == 1;
+        if (t->q2) {
+            if (one && lin2) k_matvec_q2_f32x<true, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else if (one) k_matvec_q2_f32x<false, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else if (lin2) k_matvec_q2_f32x<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else k_matvec_q2_f32x<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+        } else {
+            if (one && lin2) k_matvec_qg_f32x<true, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else if (one) k_matvec_qg_f32x<false, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else if (lin2) k_matvec_qg_f32x<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else k_matvec_qg_f32x<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+        }
+    }
+    timing_stop(tslot, st, 2 + passes);
+    return (int)cudaGetLastError();
+}
+
 int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (t->panel_ok && nrhs == 1) return launch_panel_matvec(s, const_cast<dq_terms*>(t), x, y, dtype, stream);
     if (dtype == DQ_F64) return launch_matvec_fx(s, const_cast<dq_terms*>(t), (const double*)x, (double*)y, nrhs, st);
-    return launch_matvec_t<float>(s, t, (const float*)x, (float*)y, nrhs, st);
+    return launch_matvec_f32x(s, const_cast<dq_terms*>(t), (const float*)x, (float*)y, nrhs, st);
 }
 
 }  // namespace dq

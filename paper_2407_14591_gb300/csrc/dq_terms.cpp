@@ -15,6 +15,7 @@
 // n_i n_j from NN, and a list of hops with the amplitude table sqrt((n_a + 1) n_b).
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <map>
 #include <vector>
@@ -24,6 +25,33 @@
 #include "dq_internal.h"
 
 namespace dq {
+
+// Significant bits of the FP32-path coefficients: 24, fewer when a row can have so many hops
+// that max_hops * 2^(bits + 30) would reach 2^62 (int64 hop sums of int32 x below 2^30).
+static int fp32_mbits(int max_hops) {
+    int lg = 0;
+    while ((1 << lg) < std::max(max_hops, 1)) ++lg;
+    return std::min(24, 32 - lg);
+}
+
+// Grids of the FP32 path: hop amplitudes (largest |c| = cmax_h) on 2^e_h with fp32_mbits(max_hops)
+// bits, diagonal coefficients (largest cmax_d, at most tdiag unit terms per row) on a finer 2^e_d
+// with up to 52 bits and the row's diagonal below 2^62. 0 <= e_h - e_d <= 60, so a row's hop sum
+// (int64) shifted onto the diagonal grid fits in 128 bits.
+static void fp32_grids(double cmax_h, double cmax_d, long long tdiag, int max_hops, int* e_h, int* e_d) {
+    int lg = 0;
+    while ((1ll << lg) < std::max(tdiag, 1ll)) ++lg;
+    const int bd = std::min(52, 62 - lg), bh = fp32_mbits(max_hops);
+    int eh = cmax_h > 0.0 ? std::ilogb(cmax_h) + 1 - bh : INT32_MIN / 2;
+    int ed = cmax_d > 0.0 ? std::ilogb(cmax_d) + 1 - bd : INT32_MIN / 2;
+    if (cmax_h <= 0.0 && cmax_d <= 0.0) eh = ed = 0;
+    else if (cmax_h <= 0.0) eh = ed;
+    else if (cmax_d <= 0.0) ed = eh;
+    if (ed > eh) eh = ed;            // hops far below the diagonal: their grid coarsens
+    if (eh - ed > 60) ed = eh - 60;  // diagonal far below the hops: its grid coarsens
+    *e_h = eh;
+    *e_d = ed;
+}
 
 static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms* t) {
     const int L = s->L;
@@ -175,6 +203,49 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
             if ((rc0 = dev_upload(t->dev_allocs, mp.data(), mp.size() * 8, &q))) return rc0;
             v.Mpos = (const long long*)q;
         }
+        // FP32 vectors: hop amplitudes with at most 24 bits, the diagonal on a finer grid
+        {
+            double cmax_h = 0.0, cmax_d = std::fabs(C);
+            for (int l = 0; l < nl; ++l) {
+                cmax_h = std::max(cmax_h, std::fabs(Ah[l]));
+                cmax_d = std::max(cmax_d, std::fabs(Kh[l]));
+            }
+            for (double u : lin_host) cmax_d = std::max(cmax_d, std::fabs(u));
+            for (int l = 0; l < nl; ++l) {
+                if (v.kpos[l] >= 0)
+                    for (int q2 = 0; q2 < 64; ++q2) cmax_d = std::max(cmax_d, std::fabs(pos[v.kpos[l] + q2]));
+                if (v.apos[l] >= 0)
+                    for (int q2 = 0; q2 < 64; ++q2) cmax_h = std::max(cmax_h, std::fabs(pos[v.apos[l] + q2]));
+            }
+            fp32_grids(cmax_h, cmax_d, tdiag, hops, &v.emin32, &v.emin32d);
+        }
+        auto md32 = [&](double c) { return (long long)std::llrint(std::ldexp(c, -v.emin32d)); };
+        auto mh32 = [&](double c) { return (long long)std::llrint(std::ldexp(c, -v.emin32)); };
+        v.MC32 = md32(C);
+        std::vector<long long> mka32(2 * kMaxLayers, 0);
+        for (int l = 0; l < nl; ++l) {
+            mka32[l] = md32(Kh[l]);
+            mka32[kMaxLayers + l] = mh32(Ah[l]);
+        }
+        if ((rc0 = dev_upload(t->dev_allocs, mka32.data(), mka32.size() * 8, &q))) return rc0;
+        v.MKA32 = (const long long*)q;
+        if (!lin_host.empty()) {
+            std::vector<long long> ml(64, 0);
+            for (int p = 0; p < 64; ++p) ml[p] = md32(lin_host[p]);
+            if ((rc0 = dev_upload(t->dev_allocs, ml.data(), ml.size() * 8, &q))) return rc0;
+            v.Mlin32 = (const long long*)q;
+        }
+        if (!pos.empty()) {
+            std::vector<long long> mp(pos.size(), 0);
+            for (int l = 0; l < nl; ++l) {
+                if (v.kpos[l] >= 0)
+                    for (int q2 = 0; q2 < 64; ++q2) mp[v.kpos[l] + q2] = md32(pos[v.kpos[l] + q2]);
+                if (v.apos[l] >= 0)
+                    for (int q2 = 0; q2 < 64; ++q2) mp[v.apos[l] + q2] = mh32(pos[v.apos[l] + q2]);
+            }
+            if ((rc0 = dev_upload(t->dev_allocs, mp.data(), mp.size() * 8, &q))) return rc0;
+            v.Mpos32 = (const long long*)q;
+        }
     }
     std::vector<float> kaf(2 * kMaxLayers, 0.f);
     std::vector<double> ka(2 * kMaxLayers, 0.0);
@@ -254,7 +325,6 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     std::vector<double> amp((size_t)Q * Q, 0.0);
     for (int a = 0; a < Q; ++a)
         for (int b = 0; b < Q; ++b) amp[(size_t)a * Q + b] = std::sqrt((double)((a + 1) * b));
-    v.C = 0.0;
     v.nsite = (int)site_sh.size();
     v.npair = (int)pair_K.size();
     v.nhop = (int)hop_t.size();
@@ -263,30 +333,10 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     void* p;
     if ((rc = dev_upload(t->dev_allocs, site_sh.data(), site_sh.size() * 4, &p))) return rc;
     v.site_sh = (const int*)p;
-    if ((rc = dev_upload(t->dev_allocs, site_f.data(), site_f.size() * 8, &p))) return rc;
-    v.site_f = (const double*)p;
     if ((rc = dev_upload(t->dev_allocs, pair_sh.data(), pair_sh.size() * 4, &p))) return rc;
     v.pair_sh = (const int*)p;
-    if ((rc = dev_upload(t->dev_allocs, pair_K.data(), pair_K.size() * 8, &p))) return rc;
-    v.pair_K = (const double*)p;
     if ((rc = dev_upload(t->dev_allocs, hop_sh.data(), hop_sh.size() * 4, &p))) return rc;
     v.hop_sh = (const int*)p;
-    if ((rc = dev_upload(t->dev_allocs, hop_t.data(), hop_t.size() * 8, &p))) return rc;
-    v.hop_t = (const double*)p;
-    if ((rc = dev_upload(t->dev_allocs, amp.data(), amp.size() * 8, &p))) return rc;
-    v.amp = (const double*)p;
-    v.Cf = (float)v.C;
-    auto upf = [&](const std::vector<double>& src, const float** dst) -> int {
-        std::vector<float> f(src.begin(), src.end());
-        void* q;
-        int r = dev_upload(t->dev_allocs, f.data(), f.size() * 4, &q);
-        *dst = (const float*)q;
-        return r;
-    };
-    if ((rc = upf(site_f, &v.site_ff))) return rc;
-    if ((rc = upf(pair_K, &v.pair_Kf))) return rc;
-    if ((rc = upf(hop_t, &v.hop_tf))) return rc;
-    if ((rc = upf(amp, &v.ampf))) return rc;
     // Fixed-point coefficients for FP64 vectors, as for Q = 2 (compile_q2): one exponent emin,
     // a row's diagonal (at most T_diag unit terms, a pair counting (Q-1)^2) below 2^62 in int64,
     // every hop amplitude below 2^55.
@@ -317,6 +367,29 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         if ((rc = upm(site_f, &v.Msite))) return rc;
         if ((rc = upm(pair_K, &v.Mpair))) return rc;
         if ((rc = upm(hop_amp, &v.Mhop))) return rc;
+        // FP32 vectors: hop amplitudes with at most 24 bits (int32), the diagonal on a finer grid
+        {
+            double cmax_h = 0.0, cmax_d = 0.0;
+            for (double u : hop_amp) cmax_h = std::max(cmax_h, std::fabs(u));
+            for (double u : site_f) cmax_d = std::max(cmax_d, std::fabs(u));
+            for (double u : pair_K) cmax_d = std::max(cmax_d, std::fabs(u));
+            fp32_grids(cmax_h, cmax_d, tdiag, 2 * v.nhop, &v.emin32, &v.emin32d);
+        }
+        v.MC32 = 0;
+        auto upd = [&](const std::vector<double>& src, const long long** dst) -> int {
+            std::vector<long long> m(src.size());
+            for (size_t k = 0; k < src.size(); ++k) m[k] = (long long)std::llrint(std::ldexp(src[k], -v.emin32d));
+            void* q;
+            int r = dev_upload(t->dev_allocs, m.data(), m.size() * 8, &q);
+            *dst = (const long long*)q;
+            return r;
+        };
+        std::vector<int> mh(hop_amp.size());
+        for (size_t k = 0; k < hop_amp.size(); ++k) mh[k] = (int)std::llrint(std::ldexp(hop_amp[k], -v.emin32));
+        if ((rc = upd(site_f, &v.Msite32))) return rc;
+        if ((rc = upd(pair_K, &v.Mpair32))) return rc;
+        if ((rc = dev_upload(t->dev_allocs, mh.data(), mh.size() * 4, &p))) return rc;
+        v.Mhop32 = (const int*)p;
     }
     return DQ_OK;
 }
