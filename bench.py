@@ -41,7 +41,7 @@ FALLBACK_HBM = 6800.0
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the full-size product,
     # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.24 GB read + 1.31 GB written
-    ("j1j2_square_6x5_N15", 2, "f64", 1, "b59fa4d5fb943da9"): 19.55e9,
+    ("j1j2_square_6x5_N15", 2, "f64", 1, "0f1a6f21dcad83ae"): 19.55e9,
 }
 
 WORKLOADS = {
