@@ -8,7 +8,8 @@
 //          unranks its row, evaluates the diagonal, applies every off-diagonal term, ranks each
 //          produced state and gathers x at that index: y_i = d_i x_i + sum_j h_ij x_j. Each y_i
 //          is written once by one thread, so no atomics are needed and the result is
-//          deterministic.
+//          deterministic. The sums are exact fixed point (dq_fixed.cuh): x is first scaled per
+//          column to int64 (FP64 vectors) or int32 (FP32 vectors) by a two-kernel prepass.
 #include <cstdint>
 
 #include <cuda_runtime.h>
