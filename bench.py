@@ -36,12 +36,12 @@ METRIC = "H·v sector elements/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM = 6800.0
 
-# DRAM traffic per launch of the product kernel from one ncu capture, keyed by the SHA-256 of the
-# kernel sources it was taken on; reported only while the sources are unchanged.
+# DRAM traffic per launch of the panel kernel from one ncu capture, keyed by the SHA-256 of the
+# panel kernel's sources (PANEL_SOURCES) it was taken on; reported only while they are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the full-size product,
     # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.24 GB read + 1.31 GB written
-    ("j1j2_square_6x5_N15", 2, "f64", 1, "0f1a6f21dcad83ae"): 19.55e9,
+    ("j1j2_square_6x5_N15", 2, "f64", 1, "e81f80324a6fe21d"): 19.55e9,
 }
 
 WORKLOADS = {
@@ -56,14 +56,17 @@ WORKLOADS = {
 }
 
 
+# Sources the panel kernel is built from (kernel, plan, fixed-point helpers, shared structures).
+PANEL_SOURCES = ("dq_panel.cu", "dq_panel.cpp", "dq_fixed.cuh", "dq_internal.h")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2407_14591_gb300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".h", ".cpp")):
-            with open(os.path.join(csrc, fn), "rb") as f:
-                h.update(fn.encode())
-                h.update(f.read())
+    for fn in PANEL_SOURCES:
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
