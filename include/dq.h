@@ -153,7 +153,9 @@ void dq_free_terms(dq_terms* t);
  * same route with 31-bit integers for x, hop amplitudes with 24 significant bits (int64 hop
  * sums) and the diagonal on a finer grid. An Inf or NaN in x makes y NaN and raises the sector's
  * error word (DQ_EDEVICE from dq_check_device). The call keeps a scratch area of
- * D * nrhs * 8 bytes (FP64) or 4 bytes (FP32) with the terms, allocated on first use.
+ * D * nrhs * 8 bytes (FP64) or 4 bytes (FP32) with the terms, allocated on first use (so make one
+ * call before capturing calls into a CUDA graph); calls with the same terms that overlap on the
+ * GPU (two streams at once) race on it, so order them on one stream or use separate terms.
  * Errors: DQ_EINVAL (NULL pointers, bad dtype or nrhs, terms of another sector). */
 int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
 
