@@ -143,7 +143,6 @@ struct PanelPlan {
     int nA, nK;
     long long MC, MK[kPanelMaxK], MA[kPanelMaxA];  // coefficients / 2^emin
     int emin;
-    int head32;  // FP32 input: |X| < 2^head32, so a row's int32 sum of all its hops cannot overflow
     int cmax;  // longest panel
     // per-panel source lists (built on the host): panel p owns entries [list_off[p], list_off[p+1])
     // = its active P_0 partners (first list_cnt0[p] of class 0, then class 1) and then its valid

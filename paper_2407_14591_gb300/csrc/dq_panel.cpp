@@ -160,15 +160,6 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
             P.xg_end[P.n_xg++] = nb;
         }
     }
-    {
-        // FP32 input: every hop of a row (inside P_0, inside P_1, across the cut) adds one int32
-        // value to one int32 class sum, so |X| < 2^(31 - ceil(log2(hops + 1))) cannot overflow
-        const int hops = P.p0_end[kPanelMaxA - 1] + (P.n_p1l ? P.p1l_end[P.n_p1l - 1] : 0) +
-                         (P.n_xg ? P.xg_end[P.n_xg - 1] : 0);
-        int lg = 0;
-        while ((1 << lg) < hops + 1) ++lg;
-        P.head32 = std::min(30, 31 - lg);
-    }
     P.nA = (int)Avals.size();
     P.nK = (int)Kvals.size();
     // common power of two of all coefficients

@@ -2,12 +2,10 @@
 //
 // Arithmetic. FP64 work runs at a small fraction of the integer rate on this GPU, so the sums
 // are exact integer sums: a prepass scales x by 2^F (F from the largest exponent in x) and
-// rounds it to int64 (FP64 input, |X| < 2^56) or int32 (FP32 input, |X| < 2^head32 with
-// head32 = 31 - ceil(log2(hop bonds + 1)), 24 for the 120 bonds of the 6x5 J1-J2 lattice); every
-// hop adds an integer to a per-class sum (int64, or int32 for FP32 input); the row result
-// sum_k M_k T_k (coefficients M_k = c_k / 2^emin, integers) is formed in 128-bit integers and
-// rounded once to the output type. The only error is the rounding of
-// x to 2^-F, at most 2^-57 (FP64) or 2^-(head32+1) (FP32) of max|x| per term.
+// rounds it to int64 (FP64 input, |X| < 2^56) or int32 (FP32 input, |X| < 2^30); every hop adds
+// an integer; the row result sum_k M_k T_k (coefficients M_k = c_k / 2^emin, integers) is formed
+// in 128-bit integers and rounded once to the output type. The only error is the rounding of
+// x to 2^-F, at most 2^-57 (FP64) or 2^-31 (FP32) of max|x| per term.
 //
 // Data movement. One CTA per panel (all rows with one P_0 pattern s0, contiguous in the
 // canonical order), persistent over panels. The panel of x is loaded into shared memory; hops
@@ -19,7 +17,6 @@
 // are not skipped but pointed at a slot that holds zero: no branches, and all such lanes read one
 // address. Every y element is written once, by one thread.
 #include <cstdint>
-#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -71,10 +68,10 @@ __global__ void k_exp_max(const T* __restrict__ x, uint64_t n, WsHeader* h) {
     if ((threadIdx.x & 31) == 0 && m) atomicMax(&h->emax, m);
 }
 
-// X = round(x 2^F) with F chosen from the largest exponent so that |X| < 2^xhead. 16-byte loads
+// X = round(x 2^F) with F chosen from the largest exponent so that |X| < 2^HEAD. 16-byte loads
 // and stores when x is 16-byte aligned (X always is).
 template <typename T, typename XT>
-__global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t n, int xhead, WsHeader* h) {
+__global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t n, WsHeader* h) {
     using U = typename FBits<T>::U;
     constexpr int BIAS = FBits<T>::BIAS;
     const int emax = h->emax;
@@ -82,8 +79,8 @@ __global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t
         if (blockIdx.x == 0 && threadIdx.x == 0) h->bad = 1;
         return;
     }
-    // |x| < 2^(emax - BIAS + 1), so X = x 2^F stays below 2^xhead
-    const int F = xhead - (emax - BIAS + 1);
+    // |x| < 2^(emax - BIAS + 1), so X = x 2^F stays below 2^HEAD
+    const int F = XHead<XT>::HEAD - (emax - BIAS + 1);
     if (blockIdx.x == 0 && threadIdx.x == 0) h->F = F;
     const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, step = (uint64_t)gridDim.x * blockDim.x;
     uint64_t head = 0;
@@ -258,9 +255,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
     const int tid = threadIdx.x;
     const unsigned char* own = smem + kOwn;
     uint32_t s2[E];  // P_1 pattern of each row, shifted left by one (rank-table byte offset)
-    // per-class hop sums: int64 for FP64 input, int32 for FP32 input (|X| < 2^head32 keeps them exact)
-    using AT = typename std::conditional<sizeof(XT) == 4, int, long long>::type;
-    AT acc[NA][E];
+    long long acc[NA][E];
     const uint16_t* st = P.t1states + P.t1start[pc.n1];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -281,7 +276,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 int c = tid + e * kPT;
-                if (c < pc.C) acc[k][e] += (AT)__ldg(src + c) + (AT)__ldg(src2 + c);
+                if (c < pc.C) acc[k][e] += (long long)__ldg(src + c) + (long long)__ldg(src2 + c);
             }
         }
         if (l < l1) {
@@ -289,7 +284,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 int c = tid + e * kPT;
-                if (c < pc.C) acc[k][e] += (AT)__ldg(src + c);
+                if (c < pc.C) acc[k][e] += (long long)__ldg(src + c);
             }
         }
     }
@@ -309,7 +304,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const uint32_t t = (a[e] & lb) ? (s2[e] ^ pm2) : kZeroSlot;
-                    acc[k][e] += (AT)lds_x<XT>(own, lds_u16(smem, t));
+                    acc[k][e] += lds_x<XT>(own, lds_u16(smem, t));
                 }
             }
         }
@@ -334,7 +329,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
 #pragma unroll
                 for (int e = 0; e < E; ++e) {
                     const uint32_t t = ((s2[e] ^ flip) & bb2) ? (s2[e] ^ bb2) : kZeroSlot;
-                    acc[k][e] += (AT)lds_x<XT>(sp, lds_u16(smem, t));
+                    acc[k][e] += lds_x<XT>(sp, lds_u16(smem, t));
                 }
             }
         }
@@ -361,7 +356,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
         I128 r = {0, 0};
         mac(r, md, lds_x<XT>(own, (uint32_t)(c * sizeof(XT))));
 #pragma unroll
-        for (int k = 0; k < NA; ++k) mac(r, P.MA[k], (long long)acc[k][e]);
+        for (int k = 0; k < NA; ++k) mac(r, P.MA[k], acc[k][e]);
         y[pc.start + c] = i128_to<OUT>(r, scale);
     }
 }
@@ -522,7 +517,7 @@ static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, vo
     cudaMemsetAsync(h, 0, sizeof(WsHeader), st);
     const int sms = sms_count();
     k_exp_max<T><<<sms * 8, 256, 0, st>>>(x, s->D, h);
-    k_to_fixed<T, XT><<<sms * 8, 256, 0, st>>>(x, X, s->D, sizeof(XT) == 8 ? XHead<XT>::HEAD : P.head32, h);
+    k_to_fixed<T, XT><<<sms * 8, 256, 0, st>>>(x, X, s->D, h);
     const int cap = P.cmax + 16 / (int)sizeof(XT) + 4;
     size_t sm = PanelSmem<XT>::total(cap, R);
     auto kern = k_panel<XT, T, NA, R>;
