@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libdq.so")
+# DQ_CHECKED=1 selects the checked build (device rank results compared with D; see build.py)
+LIB_PATH = os.path.join(_HERE, "libdq_checked.so" if os.environ.get("DQ_CHECKED") == "1" else "libdq.so")
 
 DQ_OK, DQ_EINVAL, DQ_ERANGE, DQ_EINDEX, DQ_ESTATE, DQ_ENOMEM, DQ_ECUDA, DQ_EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 DQ_F64, DQ_F32 = 0, 1

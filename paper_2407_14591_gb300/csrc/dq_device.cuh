@@ -23,6 +23,18 @@ __device__ __forceinline__ uint32_t field_of(const DevSector& S, uint64_t w, int
 }
 
 // Eq. (index) for a valid state. off_s / str_s may live in shared or global memory.
+// Checked builds (-DDQ_CHECKED): a rank at or beyond D raises the sector's error word and is
+// replaced by 0, so the gather that follows stays inside x. Normal builds compile this away.
+__device__ __forceinline__ uint64_t checked_rank(const DevSector& S, uint64_t j) {
+#ifdef DQ_CHECKED
+    if (j >= S.D) {
+        atomicAdd(S.err, 1);
+        return 0;
+    }
+#endif
+    return j;
+}
+
 __device__ __forceinline__ uint64_t d_rank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t w) {
     uint64_t idx = 0;
     int lam = 0;
@@ -34,14 +46,14 @@ __device__ __forceinline__ uint64_t d_rank(const DevSector& S, const uint64_t* o
         idx += off_s[o] + str_s[o] * (uint64_t)li;
         lam += n;
     }
-    return idx;
+    return checked_rank(S, idx);
 }
 
 // Lin's two-table form (Sec. 3.3): index = c_0(sigma^(0)) + index_1(sigma^(1)).
 __device__ __forceinline__ uint64_t d_rank_lin2(const DevSector& S, uint64_t w) {
     uint32_t f0 = (uint32_t)(w >> S.shift[0]);
     uint32_t f1 = (uint32_t)(w & ((1ull << (S.nb * S.Lk[1])) - 1));
-    return __ldg(S.c0_tab + f0) + (uint64_t)__ldg(S.rank_tab[S.tab[1]] + f1);
+    return checked_rank(S, __ldg(S.c0_tab + f0) + (uint64_t)__ldg(S.rank_tab[S.tab[1]] + f1));
 }
 
 // Alg. 4 for idx < D.
