@@ -40,8 +40,8 @@ FALLBACK_HBM = 6800.0
 # panel kernel's sources (PANEL_SOURCES) it was taken on; reported only while they are unchanged.
 NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the full-size product,
-    # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.24 GB read + 1.31 GB written
-    ("j1j2_square_6x5_N15", 2, "f64", 1, "e81f80324a6fe21d"): 19.55e9,
+    # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.25 GB read + 1.31 GB written
+    ("j1j2_square_6x5_N15", 2, "f64", 1, "40f026dacd629da7"): 19.56e9,
 }
 
 WORKLOADS = {

@@ -56,6 +56,22 @@ __device__ __forceinline__ uint64_t d_rank_lin2(const DevSector& S, uint64_t w) 
     return checked_rank(S, __ldg(S.c0_tab + f0) + (uint64_t)__ldg(S.rank_tab[S.tab[1]] + f1));
 }
 
+// Incremental rank (Sec. 3.2): a change of the word inside one subsystem k keeps every n_l and
+// lambda_l, so only c_k = offset_k + stride_k index_k changes and the new index is
+// i + stride_k (index_k(f') - index_k(f)): one table lookup per side instead of a full Eq. (index).
+// Q = 2 only (lambda_k is the popcount of the bits above P_k). w: the row's word, i its index,
+// w2: the word after the change.
+__device__ __forceinline__ uint64_t d_rank_within(const DevSector& S, const uint64_t* str_s, uint64_t i, uint64_t w,
+                                                  uint64_t w2, int k) {
+    const uint32_t f = field_of(S, w, k), f2 = field_of(S, w2, k);
+    const uint32_t* rt = S.rank_tab[S.tab[k]];
+    const int top = S.shift[k] + S.Lk[k];
+    const int lam = top >= 64 ? 0 : __popcll(w >> top);
+    const uint64_t st = str_s[S.os_base[k] + lam * S.os_ld[k] + __popc(f)];
+    const long long delta = (long long)__ldg(rt + f2) - (long long)__ldg(rt + f);
+    return checked_rank(S, i + (uint64_t)((long long)st * delta));
+}
+
 // Alg. 4 for idx < D.
 __device__ __forceinline__ uint64_t d_unrank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t idx) {
     uint64_t w = 0;

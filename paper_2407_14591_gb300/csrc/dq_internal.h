@@ -23,6 +23,7 @@ struct DevSector {
     uint64_t D;
     int Lk[kMaxSub];       // subsystem lengths
     int shift[kMaxSub];    // bit position of the least significant bit of P_k's field
+    signed char sub_of[64];  // subsystem holding bit position p (-1 above L * Nbits)
     int tab[kMaxSub];      // which local table P_k uses
     int nmax[kMaxSub];     // (Q-1) * L_k
     int os_base[kMaxSub];  // start of P_k's block in off / str: [lam 0..N][n 0..nmax_k+1]

@@ -10,6 +10,23 @@
 
 namespace dq {
 
+// Rank of a hopped word of row i (word s) for the Q = 2 kernels; flip = the two bits of the pair
+// (positions p and p + d). Lin's two tables (LIN2) and partitions of up to three subsystems use the
+// full rank. With four or more subsystems a pair inside one subsystem takes the incremental rank
+// (d_rank_within: one lookup per side instead of one per subsystem); measured on the 6x5 J1-J2
+// lattice it is 13 % faster with five subsystems and slower with two or three, where the extra
+// branch (lanes walk different pairs) and lookups cost more than they save.
+template <bool LIN2>
+__device__ __forceinline__ uint64_t hop_rank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s,
+                                             uint64_t i, uint64_t s, uint64_t flip, int p, int d) {
+    if (LIN2) return d_rank_lin2(S, s ^ flip);
+    if (S.n_sub >= 4) {
+        const int ka = S.sub_of[p];
+        if (ka == S.sub_of[p + d]) return d_rank_within(S, str_s, i, s, s ^ flip, ka);
+    }
+    return d_rank(S, off_s, str_s, s ^ flip);
+}
+
 // Row i of y = H x: X holds x as int64 (row-major, ld values per row, columns col0 .. col0+ch-1
 // used), the coefficients are integers times 2^emin (DevTermsQ2), sc[c] = emin - F of column
 // col0 + c. The diagonal is an int64 sum; every row result is a 128-bit sum rounded once.
@@ -58,7 +75,7 @@ __device__ __forceinline__ void row_q2_fx(const DevSector& S, const DevTermsQ2& 
             while (o) {
                 const int p = __ffsll((long long)o) - 1;
                 o &= o - 1;
-                const uint64_t j = LIN2 ? d_rank_lin2(S, s ^ (pm << p)) : d_rank(S, off_s, str_s, s ^ (pm << p));
+                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
                 const long long* Xj = X + j * ld + col0;
 #pragma unroll
                 for (int c = 0; c < CH; ++c)
@@ -72,7 +89,7 @@ __device__ __forceinline__ void row_q2_fx(const DevSector& S, const DevTermsQ2& 
             while (o) {
                 const int p = __ffsll((long long)o) - 1;
                 o &= o - 1;
-                const uint64_t j = LIN2 ? d_rank_lin2(S, s ^ (pm << p)) : d_rank(S, off_s, str_s, s ^ (pm << p));
+                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
                 const long long M = __ldg(H.Mpos + H.apos[l] + p);
                 const long long* Xj = X + j * ld + col0;
 #pragma unroll
@@ -142,7 +159,7 @@ __device__ __forceinline__ void row_q2_f32x(const DevSector& S, const DevTermsQ2
             while (o) {
                 const int p = __ffsll((long long)o) - 1;
                 o &= o - 1;
-                const uint64_t j = LIN2 ? d_rank_lin2(S, s ^ (pm << p)) : d_rank(S, off_s, str_s, s ^ (pm << p));
+                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
                 const int* Xj = X + j * ld + col0;
 #pragma unroll
                 for (int c = 0; c < CH; ++c)
@@ -155,7 +172,7 @@ __device__ __forceinline__ void row_q2_f32x(const DevSector& S, const DevTermsQ2
             while (o) {
                 const int p = __ffsll((long long)o) - 1;
                 o &= o - 1;
-                const uint64_t j = LIN2 ? d_rank_lin2(S, s ^ (pm << p)) : d_rank(S, off_s, str_s, s ^ (pm << p));
+                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
                 const long long M = __ldg(H.Mpos32 + H.apos[l] + p);
                 const int* Xj = X + j * ld + col0;
 #pragma unroll

@@ -219,6 +219,7 @@ static int build(dq_sector* s) {
 
     DevSector& v = s->dev;
     std::memset(&v, 0, sizeof v);
+    std::memset(v.sub_of, -1, sizeof v.sub_of);
     v.L = L; v.Q = Q; v.N = N; v.nb = nb; v.n_sub = s->n_sub; v.D = D;
     // partition bookkeeping and distinct table lengths
     int ntab = 0;
@@ -229,6 +230,7 @@ static int build(dq_sector* s) {
         pos += s->Lk[k];
         v.Lk[k] = s->Lk[k];
         v.shift[k] = nb * (L - pos);
+        for (int b = v.shift[k]; b < v.shift[k] + nb * s->Lk[k]; ++b) v.sub_of[b] = (signed char)k;
         v.nmax[k] = (Q - 1) * s->Lk[k];
         int t = -1;
         for (int q = 0; q < ntab; ++q)
