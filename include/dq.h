@@ -134,8 +134,9 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
 /* Which product kernel dq_matvec uses for these terms with one right-hand side: *path = 1 for the
  * panel kernel (Q = 2, two subsystems, subsystem P_1 of at most 15 sites, uniform single-site
  * fields, at most two distinct hop amplitudes and four distinct Sz Sz coefficients, dyadic
- * coefficients; exact fixed-point sums), 0 for the general kernel (any Q and partition; FP64
- * sums). Both compute the same y up to rounding. */
+ * coefficients), 0 for the general kernels (any Q, partition and nrhs). Both sum exactly in fixed
+ * point (see dq_matvec) and compute the same y up to the rounding of the coefficients to their
+ * integer grid, which is exact on the panel path. */
 int dq_terms_path(const dq_terms* t, int* path);
 
 /* Release compiled terms. NULL is allowed. */
