@@ -180,20 +180,28 @@ def test_matvec_workloads_full_fp64_and_fp32(number):
 def test_matvec_j1j2_full_size_sampled_rows(n_sub):
     """155,117,520-dimensional sector, in the launch configuration the bench times: the GPU y
     against oracle rows (gather reading) on the first and last 4096 rows and 2^16 random rows,
+    with FP64 and FP32 vectors (the FP32 product against the oracle applied to the rounded x),
     plus Hermiticity <u, H v> = <H u, v> over the whole vector."""
     w, s, x = _workload(2, n_sub=n_sub)
     o = OracleSector(w.L, w.Q, w.N, partition=s.partition)  # not cached: 2.5 GB per partition
     rng = np.random.default_rng(2)
     rows = np.concatenate([np.arange(4096), rng.choice(s.dim, 1 << 16, replace=False), np.arange(s.dim - 4096, s.dim)])
     ref = o_matvec_rows(o, w.terms, x, rows)
+    x32 = x.astype(np.float32)
+    ref32 = o_matvec_rows(o, w.terms, x32, rows)
     del o
     xt = torch.from_numpy(x).to(DEV)
     t = b.make_terms(s, w.terms)
     y = b.matvec(s, t, xt)
     torch.cuda.synchronize()
     s.check_device()
-    got = y[torch.from_numpy(rows).to(DEV)].cpu().numpy()
+    rows_d = torch.from_numpy(rows).to(DEV)
+    got = y[rows_d].cpu().numpy()
     assert maxrel(got, ref) <= TOL64
+    y32 = b.matvec(s, t, torch.from_numpy(x32).to(DEV))
+    s.check_device()
+    assert rel2(y32[rows_d].double().cpu().numpy(), ref32) <= TOL32
+    del y32
     g = torch.Generator(device="cpu").manual_seed(7)
     u = (torch.rand(s.dim, generator=g, dtype=torch.float64) * 2 - 1).to(DEV)
     Hu = b.matvec(s, t, u)
