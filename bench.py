@@ -42,6 +42,9 @@ NCU_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the full-size product,
     # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.25 GB read + 1.31 GB written
     ("j1j2_square_6x5_N15", 2, "f64", 1, "40f026dacd629da7"): 19.56e9,
+    # the same capture with FP32 vectors, profiles/k_panel_j1j2_6x5_N15_f32_traffic.md:
+    # 6.44 GB read + 0.61 GB written
+    ("j1j2_square_6x5_N15", 2, "f32", 1, "40f026dacd629da7"): 7.05e9,
 }
 
 WORKLOADS = {
