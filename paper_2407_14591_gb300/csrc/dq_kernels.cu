@@ -74,8 +74,10 @@ __global__ void __launch_bounds__(256)
     int sc[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin - hdr->F[col0 + c] : 0;
+    __shared__ uint64_t wm[kMaxLayers];
+    stage_within(S, H, wm);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
-        row_q2_fx<CH, LIN2>(S, H, off_s, str_s, i, X, ld, col0, ch, sc, y);
+        row_q2_fx<CH, LIN2>(S, H, off_s, str_s, wm, i, X, ld, col0, ch, sc, y);
 }
 
 // y = H x, general-Q operator (bosons), FP64 vectors in exact fixed point: digit functions and
@@ -159,8 +161,10 @@ __global__ void __launch_bounds__(256)
     int sc[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin32d - hdr->F[col0 + c] : 0;
+    __shared__ uint64_t wm[kMaxLayers];
+    stage_within(S, H, wm);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
-        row_q2_f32x<CH, LIN2>(S, H, off_s, str_s, i, X, ld, col0, ch, sc, y);
+        row_q2_f32x<CH, LIN2>(S, H, off_s, str_s, wm, i, X, ld, col0, ch, sc, y);
 }
 
 template <bool LIN2, int CH>
@@ -243,6 +247,17 @@ static unsigned grid_for(uint64_t n, int threads, int per_sm) {
     return (unsigned)(need < cap ? (need ? need : 1) : cap);
 }
 
+// Launches a grid-stride product kernel with 256 threads on as many blocks as can be resident at
+// once (the occupancy calculator for this kernel's registers and this launch's dynamic shared
+// memory), capped by the row count: one wave, no tail of late blocks.
+template <typename... KArgs, typename... Args>
+static void launch_resident(void (*kernel)(KArgs...), uint64_t rows, size_t smb, cudaStream_t st, Args... args) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smb) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    kernel<<<grid_for(rows, 256, per_sm), 256, smb, st>>>(args...);
+}
+
 int launch_state_at_batch(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream) {
     bool sm = os_in_smem(S);
     k_state_at<<<grid_for(n, 256, 8), 256, sm ? os_bytes(S) : 0, (cudaStream_t)stream>>>(S, d_index, d_state, n, sm);
@@ -274,7 +289,6 @@ static int launch_matvec_fx(const dq_sector* s, dq_terms* t, const double* x, do
     const bool sm = os_in_smem(S);
     const size_t smb = sm ? os_bytes(S) : 0;
     const bool lin2 = (S.n_sub == 2);
-    const unsigned grid = grid_for(S.D, 256, 8);
     const int tslot = timing_start(st);
     int passes = 0;
     for (int c0 = 0; c0 < nrhs; c0 += kMaxCh, ++passes) {
@@ -282,26 +296,26 @@ static int launch_matvec_fx(const dq_sector* s, dq_terms* t, const double* x, do
         if (t->q2) {
             if (nrhs == 1) {
                 if (lin2)
-                    k_matvec_q2_fx<true, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_q2_fx<true, 1>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
                 else
-                    k_matvec_q2_fx<false, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_q2_fx<false, 1>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
             } else {
                 if (lin2)
-                    k_matvec_q2_fx<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_q2_fx<true, kMaxCh>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
                 else
-                    k_matvec_q2_fx<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_q2_fx<false, kMaxCh>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
             }
         } else {
             if (nrhs == 1) {
                 if (lin2)
-                    k_matvec_qg_fx<true, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<true, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
                 else
-                    k_matvec_qg_fx<false, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
             } else {
                 if (lin2)
-                    k_matvec_qg_fx<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<true, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
                 else
-                    k_matvec_qg_fx<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
             }
         }
     }
@@ -327,22 +341,21 @@ static int launch_matvec_f32x(const dq_sector* s, dq_terms* t, const float* x, f
     const bool sm = os_in_smem(S);
     const size_t smb = sm ? os_bytes(S) : 0;
     const bool lin2 = (S.n_sub == 2);
-    const unsigned grid = grid_for(S.D, 256, 8);
     const int tslot = timing_start(st);
     int passes = 0;
     for (int c0 = 0; c0 < nrhs; c0 += kMaxCh, ++passes) {
         const int ch = nrhs - c0 < kMaxCh ? nrhs - c0 : kMaxCh;
         const bool one = nrhs == 1;
         if (t->q2) {
-            if (one && lin2) k_matvec_q2_f32x<true, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
-            else if (one) k_matvec_q2_f32x<false, 1><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
-            else if (lin2) k_matvec_q2_f32x<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
-            else k_matvec_q2_f32x<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            if (one && lin2) launch_resident(k_matvec_q2_f32x<true, 1>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else if (one) launch_resident(k_matvec_q2_f32x<false, 1>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else if (lin2) launch_resident(k_matvec_q2_f32x<true, kMaxCh>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+            else launch_resident(k_matvec_q2_f32x<false, kMaxCh>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
         } else {
-            if (one && lin2) k_matvec_qg_f32x<true, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
-            else if (one) k_matvec_qg_f32x<false, 1><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
-            else if (lin2) k_matvec_qg_f32x<true, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
-            else k_matvec_qg_f32x<false, kMaxCh><<<grid, 256, smb, st>>>(S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            if (one && lin2) launch_resident(k_matvec_qg_f32x<true, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else if (one) launch_resident(k_matvec_qg_f32x<false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else if (lin2) launch_resident(k_matvec_qg_f32x<true, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else launch_resident(k_matvec_qg_f32x<false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
         }
     }
     timing_stop(tslot, st, 2 + passes);

@@ -10,21 +10,45 @@
 
 namespace dq {
 
-// Rank of a hopped word of row i (word s) for the Q = 2 kernels; flip = the two bits of the pair
-// (positions p and p + d). Lin's two tables (LIN2) and partitions of up to three subsystems use the
-// full rank. With four or more subsystems a pair inside one subsystem takes the incremental rank
-// (d_rank_within: one lookup per side instead of one per subsystem); measured on the 6x5 J1-J2
-// lattice it is 13 % faster with five subsystems and slower with two or three, where the extra
-// branch (lanes walk different pairs) and lookups cost more than they save.
-template <bool LIN2>
-__device__ __forceinline__ uint64_t hop_rank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s,
-                                             uint64_t i, uint64_t s, uint64_t flip, int p, int d) {
-    if (LIN2) return d_rank_lin2(S, s ^ flip);
-    if (S.n_sub >= 4) {
-        const int ka = S.sub_of[p];
-        if (ka == S.sub_of[p + d]) return d_rank_within(S, str_s, i, s, s ^ flip, ka);
+// Per layer l, the low positions p of the pairs (p, p + dist_l) that lie inside one subsystem,
+// written by each block into shared memory (nl <= kMaxLayers words). Only partitions of three or
+// more subsystems use them: with one or two subsystems (Lin's two tables) the full rank costs no
+// more lookups than the incremental one, and every mask is left empty.
+__device__ __forceinline__ void stage_within(const DevSector& S, const DevTermsQ2& H, uint64_t* wm) {
+    for (int l = threadIdx.x; l < H.nl; l += blockDim.x) {
+        const int d = H.dist[l];
+        uint64_t w = 0;
+        if (S.n_sub >= 3)
+            for (uint64_t m = H.omask[l]; m; m &= m - 1) {
+                const int p = __ffsll((long long)m) - 1;
+                if (p + d < 64 && S.sub_of[p] == S.sub_of[p + d]) w |= 1ull << p;
+            }
+        wm[l] = w;
     }
-    return d_rank(S, off_s, str_s, s ^ flip);
+    __syncthreads();
+}
+
+// Calls f(j, p) for every active pair of one layer of row i (word s): o = the active low
+// positions, ow = those whose pair lies inside one subsystem, pm = the pair's two bits at p = 0.
+// A pair inside subsystem k changes only c_k (Sec. 3.2), so its rank is incremental
+// (d_rank_within: one rank-table lookup per side); the other pairs take the full Eq. (index)
+// (or Lin's two tables). The two kinds run as two loops rather than a branch per pair, so that
+// the lanes of a warp take the same rank form at the same time.
+template <bool LIN2, typename F>
+__device__ __forceinline__ void for_each_hop(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s,
+                                             uint64_t i, uint64_t s, uint64_t o, uint64_t ow, uint64_t pm, F&& f) {
+    if (!LIN2) {
+        for (uint64_t m = ow; m; m &= m - 1) {
+            const int p = __ffsll((long long)m) - 1;
+            f(d_rank_within(S, str_s, i, s, s ^ (pm << p), S.sub_of[p]), p);
+        }
+        o ^= ow;
+    }
+    for (uint64_t m = o; m; m &= m - 1) {
+        const int p = __ffsll((long long)m) - 1;
+        const uint64_t w2 = s ^ (pm << p);
+        f(LIN2 ? d_rank_lin2(S, w2) : d_rank(S, off_s, str_s, w2), p);
+    }
 }
 
 // Row i of y = H x: X holds x as int64 (row-major, ld values per row, columns col0 .. col0+ch-1
@@ -33,8 +57,9 @@ __device__ __forceinline__ uint64_t hop_rank(const DevSector& S, const uint64_t*
 // Layers with one hop amplitude add their gathered X in int64 and multiply once.
 template <int CH, bool LIN2>
 __device__ __forceinline__ void row_q2_fx(const DevSector& S, const DevTermsQ2& H, const uint64_t* off_s,
-                                          const uint64_t* str_s, uint64_t i, const long long* __restrict__ X, int ld,
-                                          int col0, int ch, const int* sc, double* __restrict__ y) {
+                                          const uint64_t* str_s, const uint64_t* wm, uint64_t i,
+                                          const long long* __restrict__ X, int ld, int col0, int ch, const int* sc,
+                                          double* __restrict__ y) {
     const uint64_t s = d_unrank(S, off_s, str_s, i);
     long long md = H.MC;
     if (H.Mlin) {
@@ -65,37 +90,33 @@ __device__ __forceinline__ void row_q2_fx(const DevSector& S, const DevTermsQ2& 
         if (c < ch) mac(r[c], md, __ldg(Xi + c));
     }
     for (int l = 0; l < H.nl; ++l) {
-        uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
+        const uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
         if (!o) continue;
         const uint64_t pm = 1ull | (1ull << H.dist[l]);
+        const uint64_t ow = LIN2 ? 0ull : (o & wm[l]);
         if (H.apos[l] < 0) {
             long long sum[CH];
 #pragma unroll
             for (int c = 0; c < CH; ++c) sum[c] = 0;
-            while (o) {
-                const int p = __ffsll((long long)o) - 1;
-                o &= o - 1;
-                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
+            for_each_hop<LIN2>(S, off_s, str_s, i, s, o, ow, pm, [&](uint64_t j, int) {
                 const long long* Xj = X + j * ld + col0;
 #pragma unroll
                 for (int c = 0; c < CH; ++c)
                     if (c < ch) sum[c] += __ldg(Xj + c);
-            }
+            });
             const long long MA = __ldg(H.MKA + kMaxLayers + l);
 #pragma unroll
             for (int c = 0; c < CH; ++c)
                 if (c < ch) mac(r[c], MA, sum[c]);
         } else {
-            while (o) {
-                const int p = __ffsll((long long)o) - 1;
-                o &= o - 1;
-                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
-                const long long M = __ldg(H.Mpos + H.apos[l] + p);
+            const long long* Mp = H.Mpos + H.apos[l];
+            for_each_hop<LIN2>(S, off_s, str_s, i, s, o, ow, pm, [&](uint64_t j, int p) {
+                const long long M = __ldg(Mp + p);
                 const long long* Xj = X + j * ld + col0;
 #pragma unroll
                 for (int c = 0; c < CH; ++c)
                     if (c < ch) mac(r[c], M, __ldg(Xj + c));
-            }
+            });
         }
     }
     double* yi = y + i * ld + col0;
@@ -121,8 +142,9 @@ __device__ __forceinline__ void add_i64_shl(I128& a, long long v, int sh) {
 // once to FP32 with sc = emin32d - F.
 template <int CH, bool LIN2>
 __device__ __forceinline__ void row_q2_f32x(const DevSector& S, const DevTermsQ2& H, const uint64_t* off_s,
-                                            const uint64_t* str_s, uint64_t i, const int* __restrict__ X, int ld,
-                                            int col0, int ch, const int* sc, float* __restrict__ y) {
+                                            const uint64_t* str_s, const uint64_t* wm, uint64_t i,
+                                            const int* __restrict__ X, int ld, int col0, int ch, const int* sc,
+                                            float* __restrict__ y) {
     const uint64_t s = d_unrank(S, off_s, str_s, i);
     long long md = H.MC32;
     if (H.Mlin32) {
@@ -149,36 +171,32 @@ __device__ __forceinline__ void row_q2_f32x(const DevSector& S, const DevTermsQ2
 #pragma unroll
     for (int c = 0; c < CH; ++c) hs[c] = 0;
     for (int l = 0; l < H.nl; ++l) {
-        uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
+        const uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
         if (!o) continue;
         const uint64_t pm = 1ull | (1ull << H.dist[l]);
+        const uint64_t ow = LIN2 ? 0ull : (o & wm[l]);
         if (H.apos[l] < 0) {
             long long sum[CH];
 #pragma unroll
             for (int c = 0; c < CH; ++c) sum[c] = 0;
-            while (o) {
-                const int p = __ffsll((long long)o) - 1;
-                o &= o - 1;
-                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
+            for_each_hop<LIN2>(S, off_s, str_s, i, s, o, ow, pm, [&](uint64_t j, int) {
                 const int* Xj = X + j * ld + col0;
 #pragma unroll
                 for (int c = 0; c < CH; ++c)
                     if (c < ch) sum[c] += __ldg(Xj + c);
-            }
+            });
             const long long MA = __ldg(H.MKA32 + kMaxLayers + l);
 #pragma unroll
             for (int c = 0; c < CH; ++c) hs[c] += MA * sum[c];
         } else {
-            while (o) {
-                const int p = __ffsll((long long)o) - 1;
-                o &= o - 1;
-                const uint64_t j = hop_rank<LIN2>(S, off_s, str_s, i, s, pm << p, p, H.dist[l]);
-                const long long M = __ldg(H.Mpos32 + H.apos[l] + p);
+            const long long* Mp = H.Mpos32 + H.apos[l];
+            for_each_hop<LIN2>(S, off_s, str_s, i, s, o, ow, pm, [&](uint64_t j, int p) {
+                const long long M = __ldg(Mp + p);
                 const int* Xj = X + j * ld + col0;
 #pragma unroll
                 for (int c = 0; c < CH; ++c)
                     if (c < ch) hs[c] += M * __ldg(Xj + c);
-            }
+            });
         }
     }
     const int* Xi = X + i * ld + col0;
