@@ -1,5 +1,6 @@
-// The row computation of the Q = 2 product for FP64 vectors in exact fixed point, shared by the
-// single-sector and the batched kernels.
+// The row computations of the general Q = 2 product kernels in exact fixed point (FP64 vectors
+// with int64 x and 128-bit rows, FP32 vectors with int32 x and int64 hop sums), and the walk over
+// a bond layer's active pairs with the rank form each pair needs.
 #pragma once
 
 #include <cstdint>
