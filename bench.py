@@ -39,11 +39,10 @@ FALLBACK_HBM = 6800.0
 # DRAM traffic per launch of the panel kernel from one ncu capture, keyed by the SHA-256 of the
 # panel kernel's sources (PANEL_SOURCES) it was taken on; reported only while they are unchanged.
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass) on the full-size product,
-    # profiles/k_panel_j1j2_6x5_N15_f64_traffic.md: 18.25 GB read + 1.31 GB written
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), k_panel on the full-size
+    # J1-J2 6x5 N = 15 product with FP64 vectors: 18.25 GB read + 1.31 GB written
     ("j1j2_square_6x5_N15", 2, "f64", 1, "40f026dacd629da7"): 19.56e9,
-    # the same capture with FP32 vectors, profiles/k_panel_j1j2_6x5_N15_f32_traffic.md:
-    # 6.44 GB read + 0.61 GB written
+    # the same capture with FP32 vectors: 6.44 GB read + 0.61 GB written
     ("j1j2_square_6x5_N15", 2, "f32", 1, "40f026dacd629da7"): 7.05e9,
 }
 
@@ -159,8 +158,47 @@ def aggregate(ms_local: float, rows_local: int, steps: int, reduce_max=None, red
     return ms, rows * steps / (ms / 1e3)
 
 
-def oracle_rows_rate(w, partition, x, seconds: float, steps: int | None = None, warmup: int = 0):
-    """Time the oracle's gather form on bounded row samples; returns (rows/s, rows timed, note)."""
+def _shm_put(arr):
+    from multiprocessing import shared_memory
+
+    shm = shared_memory.SharedMemory(create=True, size=max(1, arr.nbytes))
+    view = np.ndarray(arr.shape, dtype=arr.dtype, buffer=shm.buf)
+    view[...] = arr
+    return shm, (shm.name, arr.shape, arr.dtype.str)
+
+
+def _oracle_worker(task):
+    """Worker process of the all-cores oracle timing: attach the shared sector and x, and run the
+    oracle's gather form on this worker's rows. Returns (rows done, seconds)."""
+    from multiprocessing import shared_memory
+
+    from oracle import OracleSector, matvec_rows
+
+    (L, Q, N, part, terms, descs, rows) = task
+    shms, arrs = [], []
+    for name, shape, dt in descs:
+        shm = shared_memory.SharedMemory(name=name)
+        shms.append(shm)
+        arrs.append(np.ndarray(shape, dtype=np.dtype(dt), buffer=shm.buf))
+    basis, keys, x = arrs
+    o = OracleSector.from_arrays(L, Q, N, part, basis, keys)
+    t0 = time.perf_counter()
+    matvec_rows(o, terms, x, rows)
+    el = time.perf_counter() - t0
+    del o, basis, keys, x, arrs
+    for shm in shms:
+        shm.close()
+    return len(rows), el
+
+
+def oracle_rows_rate(w, partition, x, seconds: float, steps: int | None = None, warmup: int = 0,
+                     all_cores: bool = True):
+    """Time the oracle's gather form (as it stands) on bounded random-row samples of the workload:
+    on one core, and (all_cores) on all host cores, the same sample size per core split into
+    row-disjoint ranges over spawned worker processes that share the sector and x through shared
+    memory. Returns a dict with the rates (rows/s), the rows timed and the untimed build time."""
+    import multiprocessing as mp
+
     from oracle import OracleSector, matvec_rows
 
     t0 = time.perf_counter()
@@ -183,7 +221,35 @@ def oracle_rows_rate(w, partition, x, seconds: float, steps: int | None = None, 
         matvec_rows(o, w.terms, x, rng.choice(o.dim, rows_per, replace=False))
         done += rows_per
     el = time.perf_counter() - t0
-    return done / el, done, el, setup, rows_per
+    out = {"rate1": done / el, "rows1": done, "s1": el, "setup": setup, "rows_per_step": rows_per,
+           "steps": n_steps, "cores": 1}
+    ncores = os.cpu_count() or 1
+    if all_cores and ncores > 1:
+        shms, descs = [], []
+        try:
+            for arr in (o.basis, o.keys, np.ascontiguousarray(x)):
+                shm, d = _shm_put(arr)
+                shms.append(shm)
+                descs.append(d)
+            ctx = mp.get_context("spawn")
+            with ctx.Pool(ncores) as pool:
+                # one untimed round so that every worker has imported the oracle
+                pool.map(_oracle_worker, [(w.L, w.Q, w.N, partition, w.terms, descs,
+                                           np.arange(c, o.dim, max(1, o.dim // 64))[:64]) for c in range(ncores)])
+                done_all = 0
+                t0 = time.perf_counter()
+                for _ in range(n_steps):
+                    rows = np.sort(rng.choice(o.dim, min(o.dim, rows_per * ncores), replace=False))
+                    chunks = np.array_split(rows, ncores)  # row-disjoint ranges, one per worker
+                    res = pool.map(_oracle_worker, [(w.L, w.Q, w.N, partition, w.terms, descs, c) for c in chunks])
+                    done_all += sum(r[0] for r in res)
+                el_all = time.perf_counter() - t0
+            out.update({"rate_all": done_all / el_all, "rows_all": done_all, "s_all": el_all, "cores": ncores})
+        finally:
+            for shm in shms:
+                shm.close()
+                shm.unlink()
+    return out
 
 
 def lanczos_check(b, torch):
@@ -203,7 +269,7 @@ def lanczos_check(b, torch):
     s = b.make_sector(w.L, w.Q, w.N, w.n_sub)
     w, x = wl.workload(1, D=s.dim)
     t = b.make_terms(s, w.terms)
-    out = {"workload": w.name, "D": s.dim, "steps": steps, "E0_oracle": e_ref}
+    out = {"workload": w.name, "D": s.dim, "steps": steps, "E0_oracle": e_ref, "reorth": True}
     for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
         v0 = torch.from_numpy(x).to("cuda", dt)
         b.lanczos(s, t, v0, steps)
@@ -211,8 +277,16 @@ def lanczos_check(b, torch):
         t0 = time.perf_counter()
         r = b.lanczos(s, t, v0, steps)
         el = time.perf_counter() - t0
+        # the same number of products alone (CUDA events), for the cost of the rest of the step
+        y = torch.empty_like(v0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(r["steps_done"]):
+            b.matvec(s, t, v0, y)
+        e1.record()
+        torch.cuda.synchronize()
         out[name] = {"E0": r["E0"], "rel_err": abs(r["E0"] - e_ref) / abs(e_ref), "ms": 1e3 * el,
-                     "steps_done": r["steps_done"]}
+                     "steps_done": r["steps_done"], "products_ms": e0.elapsed_time(e1)}
     return out
 
 
@@ -227,16 +301,19 @@ def run_reference(args, world, rank):
     part = most_equal_partition(w.L, w.n_sub, w.Q)
     D = sector_dim(w.L, w.Q, w.N)
     w, x = wl.workload(number, n_sub=args.n_sub, D=D)
-    rate, done, el, setup, per = oracle_rows_rate(w, part, x, seconds=max(10.0, 2.0 * args.steps), steps=args.steps,
-                                                  warmup=args.warmup)
+    r = oracle_rows_rate(w, part, x, seconds=max(8.0, 1.0 * args.steps), steps=args.steps, warmup=args.warmup)
+    rate = r.get("rate_all", r["rate1"])
+    el = r.get("s_all", r["s1"])
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "elements/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "D": D, "n_sub": w.n_sub, "partition": part, "nrhs": 1},
-        "cpu_baseline": {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{per} random rows per step (gather form), {args.steps} steps, "
-                                   f"after a {setup:.0f} s untimed sector build (enumerate + sort)"},
+        "cpu_baseline": {"value": rate, "unit": "elements/s", "cores": r["cores"], "kind": "oracle",
+                         "sample": f"{r.get('rows_all', r['rows1']) // args.steps} random rows per step (gather form), "
+                                   f"{args.steps} steps over {r['cores']} processes with row-disjoint ranges, "
+                                   f"after a {r['setup']:.0f} s untimed sector build (enumerate + sort)",
+                         "single_core": {"value": r["rate1"], "cores": 1, "rows": r["rows1"]}},
         "e2e": {"value": rate, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -438,30 +515,49 @@ def run_rank(args, world, rank, local, dist, torch):
 
 
 def run_lanczos(args, world, rank, local, dist, torch):
-    """Workload 2's Lanczos form at full size: the same seeded start vector with FP64 vectors and
-    with FP32 vectors (FP64 alpha/beta recurrence and dot products in both), plain three-term
-    recurrence (full re-orthogonalisation would cost D*k FP64 operations per step here).
-    One JSON line: E0 of both, their relative difference, time per Lanczos step."""
+    """The Lanczos form of workload 2 (J1-J2 6x5, N = 15, D = 155,117,520) or, with
+    --lanczos-workload bose, workload 3 (Bose-Hubbard Q = 4, L = 14, N = 14, D = 6,472,168), at
+    full size: the same seeded start vector with FP64 vectors and with FP32 vectors (FP64
+    recurrence, dot products and updates in both), full re-orthogonalisation (classical
+    Gram-Schmidt twice per step). One JSON line: E0 of both, their relative difference, the
+    residual ||H psi - E0 psi|| / |E0| of each Ritz vector (FP64), time per Lanczos step, and the
+    product's share of it."""
     from paper_2407_14591_gb300 import binding as b
 
     steps = args.lanczos_steps
-    w, s, x_np = build_workload(2, args.n_sub, args.N)
+    number = {"j1j2": 2, "bose": 3}[args.lanczos_workload]
+    w, s, x_np = build_workload(number, args.n_sub if number == 2 else None, args.N if number == 2 else None)
     t = b.make_terms(s, w.terms)
     out = {}
     for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
         v0 = torch.from_numpy(x_np).to("cuda", dt)
-        b.lanczos(s, t, v0, 3, reorth=False)  # warm-up (scratch, tables)
+        b.lanczos(s, t, v0, 3, reorth=True)  # warm-up (scratch, tables)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = b.lanczos(s, t, v0, steps, reorth=False)
+        r = b.lanczos(s, t, v0, steps, reorth=True, want_vector=True)
         el = time.perf_counter() - t0
-        out[name] = {"E0": r["E0"], "steps_done": r["steps_done"], "ms_per_step": 1e3 * el / max(r["steps_done"], 1)}
-        del v0
+        psi = r.pop("psi")
+        hpsi = b.matvec(s, t, psi)
+        res = (torch.linalg.norm(hpsi.double() - r["E0"] * psi.double()) / abs(r["E0"])).item()
+        del hpsi, psi
+        # the products alone: `steps` products of the same vector, CUDA events
+        y = torch.empty_like(v0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(r["steps_done"]):
+            b.matvec(s, t, v0, y)
+        e1.record()
+        torch.cuda.synchronize()
+        prod_ms = e0.elapsed_time(e1)
+        out[name] = {"E0": r["E0"], "steps_done": r["steps_done"], "ms_per_step": 1e3 * el / max(r["steps_done"], 1),
+                     "residual": res, "products_ms_per_step": prod_ms / max(r["steps_done"], 1),
+                     "total_s": el}
+        del v0, y
     rel = abs(out["f32"]["E0"] - out["f64"]["E0"]) / abs(out["f64"]["E0"])
     if rank == 0:
         print(json.dumps({"metric": "Lanczos E0, FP32 vectors vs FP64 vectors", "value": rel, "unit": "relative",
                           "higher_is_better": False, "n_gpus": world, "steps": steps, "data": "synthetic",
-                          "config": {"workload": w.name, "D": s.dim, "n_sub": s.n_sub, "reorth": False},
+                          "config": {"workload": w.name, "D": s.dim, "n_sub": s.n_sub, "reorth": True},
                           "f64": out["f64"], "f32": out["f32"]}), flush=True)
 
 
@@ -479,7 +575,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the workload-1 Lanczos E0 check")
-    ap.add_argument("--lanczos-steps", type=int, default=40, help="steps of --workload lanczos")
+    ap.add_argument("--lanczos-steps", type=int, default=100, help="steps of --workload lanczos")
+    ap.add_argument("--lanczos-workload", default="j1j2", choices=["j1j2", "bose"],
+                    help="sector of --workload lanczos: workload 2 (j1j2) or workload 3 (bose)")
     ap.add_argument("--graph", type=int, default=0,
                     help="also time this many products captured in one CUDA graph (launch-free rate)")
     args = ap.parse_args()
@@ -659,11 +757,13 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline and args.nrhs == 1:
-        rate, done, el, setup, per = oracle_rows_rate(w, s.partition, x_np if x_np.ndim == 1 else x_np[:, 0],
-                                                      seconds=12.0)
-        cpu = {"value": rate, "unit": "elements/s", "cores": 1, "kind": "oracle",
-               "sample": f"{done} random rows in {el:.1f} s (gather form, numpy single thread), after a "
-                         f"{setup:.0f} s untimed sector build"}
+        r = oracle_rows_rate(w, s.partition, x_np if x_np.ndim == 1 else x_np[:, 0], seconds=8.0)
+        rate = r.get("rate_all", r["rate1"])
+        cpu = {"value": rate, "unit": "elements/s", "cores": r["cores"], "kind": "oracle",
+               "sample": f"{r.get('rows_all', r['rows1']) // r['steps']} random rows per step, {r['steps']} steps (gather form, "
+                         f"numpy), over {r['cores']} spawned processes with row-disjoint ranges, after a "
+                         f"{r['setup']:.0f} s untimed sector build",
+               "single_core": {"value": r["rate1"], "cores": 1, "rows": r["rows1"], "seconds": r["s1"]}}
 
     lz = lanczos_check(b, torch) if rank == 0 and not args.no_lanczos else None
 

@@ -170,8 +170,12 @@ int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int
  * 64 MiB that every GPU loading this library reserves until the process exits. Hence the limit:
  * D <= 8,388,568 for DQ_F64 and D <= 16,777,144 for DQ_F32; larger sectors return DQ_ERANGE with
  * the limit in dq_last_error(). Only terms on the panel path (dq_terms_path == 1) are served;
- * others return DQ_EINVAL. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) and caches it; make that first call before any stream capture. Every
+ * others return DQ_EINVAL. The first call on a device does a one-time set-up: it looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it. With CUDA's default lazy module
+ * loading, that lookup is also when the runtime loads the code module holding the array, so the
+ * 64 MiB are taken from the device at that first call, not when the library is loaded: make the
+ * first call on each device before handing the device's memory to a pool of your own, and
+ * before any stream capture. Later calls allocate nothing. Every
  * call reuses the same array, and each call clears the header part it needs to start at zero;
  * calls that overlap on the GPU (for example on two streams at once) race on the array and give
  * wrong results, so order them on one stream or synchronise between them. x and y: device
@@ -231,18 +235,28 @@ void dq_batch_free(dq_batch* b);
 
 /* Ground-state energy by Lanczos (Sec. 4.4, App. D): starting from v0 (device, D elements of
  * `dtype`, normalised inside the call, not modified), run up to `steps` steps of
- *   w = H v_k; alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1};
- *   (reorth != 0) re-orthogonalise w against all earlier v by classical Gram-Schmidt, twice;
+ *   w = H v_k; alpha_k = <v_k, w>;
+ *   reorth == 0: w -= alpha_k v_k + beta_{k-1} v_{k-1} (the plain three-term recurrence);
+ *   reorth != 0: full re-orthogonalisation by classical Gram-Schmidt applied twice,
+ *                w -= V (V^T w), w -= V (V^T w), V = [v_0 .. v_k]; the first pass's coefficient
+ *                of v_k is alpha_k, and in exact arithmetic the first pass subtracts the same
+ *                alpha_k v_k + beta_{k-1} v_{k-1} as the three-term step;
  *   beta_k = ||w||; v_{k+1} = w / beta_k.
- * Dot products and norms accumulate in FP64 whatever `dtype` is; the Lanczos vectors are
- * stored in `dtype`. E0 is the smallest eigenvalue of the tridiagonal matrix, found on the host
- * by bisection on its Sturm sequence. The call stops early, without error, when
- * beta_k < 1e-14 * ||T||; *steps_done then holds the number of steps taken. alpha and beta
- * (host, room for `steps` doubles each, may be NULL) receive the recurrence coefficients.
- * The workspace ((steps+1) vectors plus scratch) is allocated and freed by the call.
- * Synchronous: returns when E0 is known. Errors: DQ_EINVAL, DQ_ENOMEM, DQ_ECUDA. */
+ * Dot products, norms and the vector updates are computed in FP64 whatever `dtype` is; the
+ * Lanczos vectors are stored in `dtype`. E0 is the smallest eigenvalue of the tridiagonal matrix
+ * T, found on the host by bisection on its Sturm sequence. The call stops early, without error,
+ * when beta_k < 1e-14 * ||T||; *steps_done then holds the number of steps taken m. alpha and
+ * beta (host, room for `steps` doubles each, may be NULL) receive the recurrence coefficients.
+ * psi (device, D elements of `dtype`, may be NULL) receives the Ritz vector of E0,
+ * sum_k y_k v_k with y the unit eigenvector of T for E0 (inverse iteration on T, sign chosen so
+ * that its largest component is positive); ||H psi - E0 psi|| is the residual of E0.
+ * The workspace ((steps+1) vectors of D elements plus scratch) is allocated and freed by the
+ * call, and the product's own scratch is kept with the terms (see dq_matvec).
+ * Synchronous: returns when E0 (and psi) are known; one host synchronisation per step. Errors:
+ * DQ_EINVAL (NULL or out-of-range arguments, steps > 4096 with reorth, a zero or non-finite v0),
+ * DQ_ENOMEM, DQ_ECUDA. */
 int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0, int steps, int dtype, int reorth,
-               double* E0, double* alpha, double* beta, int* steps_done, void* stream);
+               double* E0, double* alpha, double* beta, int* steps_done, void* psi, void* stream);
 
 /* ---- kernel timing ------------------------------------------------------------------------ */
 

@@ -212,6 +212,16 @@ class OracleSector:
             raise ValueError("partition must cover the L sites with non-empty parts")
         self.basis, self.keys = canonical_basis(L, Q, N, self.partition)
 
+    @classmethod
+    def from_arrays(cls, L: int, Q: int, N: int, partition: list[int], basis: np.ndarray, keys: np.ndarray):
+        """The same sector from the canonical basis and keys of an instance built earlier (for
+        example in another process, shared through shared memory): nothing is enumerated again."""
+        self = cls.__new__(cls)
+        self.L, self.Q, self.N, self.nb = L, Q, N, nbits_for(Q)
+        self.partition = list(partition)
+        self.basis, self.keys = basis, keys
+        return self
+
     @property
     def dim(self) -> int:
         return int(self.basis.shape[0])

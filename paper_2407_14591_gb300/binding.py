@@ -72,7 +72,7 @@ def _load() -> ctypes.CDLL:
         "dq_batch_free": (None, [vp]),
         "dq_term_grads": (i32, [vp, P(_Term), i32, vp, vp, i32, i32, vp, vp]),
         "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
-                             P(ctypes.c_double), P(i32), vp]),
+                             P(ctypes.c_double), P(i32), vp, vp]),
         "dq_timing_enable": (i32, [i32]),
         "dq_timing_read": (i32, [P(ctypes.c_double), P(ctypes.c_longlong), P(ctypes.c_longlong)]),
     }
@@ -341,8 +341,11 @@ def make_batch(sectors, terms, nrhs: int, dtype) -> Batch:
     return Batch(sectors, terms, nrhs, dtype)
 
 
-def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True) -> dict:
-    """Ground-state energy by Lanczos (synchronous). Returns E0, alpha, beta, steps_done."""
+def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True, want_vector: bool = False) -> dict:
+    """Ground-state energy by Lanczos (synchronous). Returns E0, alpha, beta, steps_done and, with
+    ``want_vector``, the Ritz vector of E0 as ``psi`` (a CUDA tensor like v0)."""
+    import torch
+
     _check_vec(sector, v0, "v0")
     if v0.dim() != 1:
         raise ValueError("v0 must be one vector")
@@ -350,10 +353,15 @@ def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True) -
     alpha = (ctypes.c_double * max(1, steps))()
     beta = (ctypes.c_double * max(1, steps))()
     done = ctypes.c_int()
+    psi = torch.empty_like(v0) if want_vector else None
     _check(_lib.dq_lanczos(sector.handle, terms.handle, ctypes.c_void_p(v0.data_ptr()), steps, _dtype_code(v0),
-                           1 if reorth else 0, ctypes.byref(E0), alpha, beta, ctypes.byref(done), _stream_handle()))
+                           1 if reorth else 0, ctypes.byref(E0), alpha, beta, ctypes.byref(done),
+                           ctypes.c_void_p(psi.data_ptr() if psi is not None else 0), _stream_handle()))
     m = done.value
-    return {"E0": E0.value, "alpha": np.array(alpha[:m]), "beta": np.array(beta[:m]), "steps_done": m}
+    out = {"E0": E0.value, "alpha": np.array(alpha[:m]), "beta": np.array(beta[:m]), "steps_done": m}
+    if psi is not None:
+        out["psi"] = psi
+    return out
 
 
 def timing_enable(on: bool = True):

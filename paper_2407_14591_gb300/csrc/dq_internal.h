@@ -222,6 +222,12 @@ void timing_stop(int slot, cudaStream_t st, int kernels);
 
 // device memory helpers; without a CUDA device dev_upload returns DQ_OK and a NULL pointer
 bool device_present();
+// SM count of the current device, cached per device index (thread-safe)
+int sm_count_cached();
+// resident blocks per SM of `kernel` with `threads` threads and `smem` bytes of dynamic shared
+// memory on the current device, from the occupancy calculator, cached per (kernel, threads,
+// smem, device); at least 1
+int occupancy_cached(const void* kernel, int threads, size_t smem);
 int dev_upload(std::vector<void*>& allocs, const void* host, size_t bytes, void** dptr);
 
 }  // namespace dq

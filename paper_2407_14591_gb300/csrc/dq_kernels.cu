@@ -227,16 +227,7 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-static int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
+static int num_sms() { return sm_count_cached(); }
 
 static inline size_t os_bytes(const DevSector& S) { return (size_t)S.os_total * 16; }
 static inline bool os_in_smem(const DevSector& S) { return os_bytes(S) <= 48 * 1024; }
@@ -249,12 +240,10 @@ static unsigned grid_for(uint64_t n, int threads, int per_sm) {
 
 // Launches a grid-stride product kernel with 256 threads on as many blocks as can be resident at
 // once (the occupancy calculator for this kernel's registers and this launch's dynamic shared
-// memory), capped by the row count: one wave, no tail of late blocks.
+// memory, cached per kernel and size), capped by the row count: one wave, no tail of late blocks.
 template <typename... KArgs, typename... Args>
 static void launch_resident(void (*kernel)(KArgs...), uint64_t rows, size_t smb, cudaStream_t st, Args... args) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 256, smb) != cudaSuccess || per_sm < 1)
-        per_sm = 1;
+    const int per_sm = occupancy_cached(reinterpret_cast<const void*>(kernel), 256, smb);
     kernel<<<grid_for(rows, 256, per_sm), 256, smb, st>>>(args...);
 }
 

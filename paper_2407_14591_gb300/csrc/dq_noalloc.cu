@@ -2,8 +2,11 @@
 // callers that must not allocate device memory while they run (see include/dq.h).
 //
 // The scratch holds the workspace header and the fixed-point copy of x that the panel kernel
-// reads (dq_panel.cu). The array is static: it is reserved when the library's device code is
-// loaded on a GPU and stays reserved until the process exits. Host code never dereferences the
+// reads (dq_panel.cu). The array is static: it is reserved when the code module that holds it
+// is loaded on a GPU and stays reserved until the process exits. Under CUDA's default lazy
+// module loading this file's module (it has no kernels of its own) is loaded by the first
+// cudaGetSymbolAddress on each device, i.e. inside the first dq_matvec_noalloc call there, which
+// is therefore the call that takes the 64 MiB from the device. Host code never dereferences the
 // symbol; it asks the runtime for the array's device address once per device and passes that
 // address to the kernels.
 #include <cstring>

@@ -498,16 +498,7 @@ size_t panel_scratch_bytes(const dq_sector* s, int dtype) {
     return 256 + ((size_t)(s->D + 8) * es + 255) / 256 * 256;
 }
 
-static int sms_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
-    return sms;
-}
+static int sms_count() { return sm_count_cached(); }
 
 template <typename T, typename XT, int NA, int R>
 static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {

@@ -107,3 +107,34 @@ def test_workload4_tune_and_graph_replay(workload4):
     # rows are computed by one thread each in a fixed order: every launch shape gives the same bits
     for a, c in zip(y0, y1):
         assert torch.equal(a, c)
+
+
+@pytest.mark.slow
+def test_workload4_largest_sectors_against_oracle_rows(workload4):
+    """The four largest sectors of the 64-chain draw, in the batched launch: oracle rows (gather
+    reading, FP64) on the first and last 4096 rows and 2^16 random rows of each, for all eight
+    right-hand sides, with FP64 and FP32 vectors (FP32 against the oracle applied to the rounded x)."""
+    from oracle import matvec_rows as o_matvec_rows
+
+    ws, secs, terms, xs = workload4
+    order = np.argsort([s.dim for s in secs])[::-1][:4]
+    for dtype in (torch.float64, torch.float32):
+        batch = b.make_batch(secs, terms, 8, dtype)
+        xt = [torch.from_numpy(x).to(DEV, dtype) for x in xs]
+        yt = [torch.empty_like(x) for x in xt]
+        batch.matvec(xt, yt)
+        torch.cuda.synchronize()
+        for k in order:
+            w, s = ws[k], secs[k]
+            o = OracleSector(w.L, 2, w.N, partition=s.partition)
+            rng = np.random.default_rng(int(k))
+            rows = np.unique(np.concatenate([np.arange(4096), rng.choice(s.dim, 1 << 16, replace=False),
+                                             np.arange(s.dim - 4096, s.dim)]))
+            xin = xt[k].double().cpu().numpy()
+            ref = o_matvec_rows(o, w.terms, xin, rows)
+            got = yt[k][torch.from_numpy(rows).to(DEV)].double().cpu().numpy()
+            del o
+            if dtype == torch.float64:
+                assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (k, w.L, w.N)
+            else:
+                assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), (k, w.L, w.N)

@@ -76,3 +76,40 @@ def test_general_nonfinite_input_gives_nan_and_error_word():
         s.check_device()
     assert e.value.code == b.DQ_EDEVICE
     s.check_device()
+
+
+@pytest.mark.parametrize("path", ["panel", "general"])
+def test_graded_column_elementwise_bound(path):
+    """One column whose entries span twenty decades (|x_i| = 10^-20u, u ~ U[0, 1], random signs):
+    every y_i meets the element-wise bound of the block fixed-point FP64 form,
+        |y_i - y_ref,i| <= 2^-52 |y_ref,i| + 2^-50 max_j|x_j| (sum_j |h_ij| + n_i max|h|),
+    n_i the nonzeros of row i, i.e. the error is absolute in units of the column maximum, not
+    relative to |y_i|. The element-wise relative errors are printed for the record."""
+    rng = np.random.default_rng(17)
+    L, N = 14, 7
+    if path == "panel":
+        terms = wl.heisenberg_terms(wl.chain_bonds(L), 1.0, 1.0) + wl.field_terms(np.full(L, 0.375))
+        n_sub = 2
+    else:
+        terms = xxz_terms(L, rng)
+        n_sub = 3
+    s = b.make_sector(L, 2, N, n_sub)
+    t = b.make_terms(s, terms)
+    assert t.path == path
+    o = OracleSector(L, 2, N, partition=s.partition)
+    H = o_matvec(o, terms, np.eye(o.dim))
+    x = 10.0 ** (-20.0 * rng.uniform(0, 1, o.dim)) * rng.choice([-1.0, 1.0], o.dim)
+    x[rng.integers(o.dim)] = 1.0
+    ref = o_matvec(o, terms, x)
+    y = b.matvec(s, t, torch.from_numpy(x).to(DEV)).cpu().numpy()
+    s.check_device()
+    absH = np.abs(H)
+    bound = 2.0 ** -52 * np.abs(ref) + 2.0 ** -50 * np.max(np.abs(x)) * (
+        absH.sum(axis=1) + (absH > 0).sum(axis=1) * absH.max())
+    err = np.abs(y - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+    rel = err / np.maximum(np.abs(ref), 1e-300)
+    big = np.abs(ref) >= 1e-3 * np.max(np.abs(ref))
+    print(f"{path}: element-wise relative error: median {np.median(rel):.1e}, max {rel.max():.1e}; "
+          f"over |y_i| >= 1e-3 max|y|: max {rel[big].max():.1e}; smallest |y_i| {np.abs(ref).min():.1e}")
+    assert rel[big].max() <= 1e-11

@@ -248,3 +248,30 @@ def test_lanczos_golden_workload1_matches_sparse_eigensolver():
     H = sps.csr_matrix((np.full(r_idx.size, 0.5), (r_idx, c_idx)), shape=(states.size,) * 2) + sps.diags(diag)
     ev = eigsh(H, k=1, which="SA", tol=1e-13)[0][0]
     assert abs(E0 - ev) <= 1e-9 * abs(ev)
+
+
+@pytest.mark.parametrize("L,Q,N,n_sub,nb", [(8, 2, 4, 2, 10), (9, 2, 3, 3, 12), (6, 3, 6, 2, 7), (5, 4, 7, 2, 6),
+                                             (6, 3, 4, 6, 6)])
+def test_diagonal_equals_kronecker_diagonal(L, Q, N, n_sub, nb):
+    """oracle.diagonal(sector, terms) is <sigma|H|sigma> of the restricted Kronecker-built H, for
+    the whole basis and for a subset of words given explicitly."""
+    rng = np.random.default_rng(2000 + L * 10 + Q)
+    terms = random_terms(rng, L, Q, nb)
+    sec = OracleSector(L, Q, N, n_sub=n_sub)
+    ref = np.diag(restricted(sec, terms))
+    np.testing.assert_allclose(oh.diagonal(sec, terms), ref, rtol=0, atol=1e-13)
+    pick = rng.choice(sec.dim, min(sec.dim, 17), replace=False)
+    np.testing.assert_allclose(oh.diagonal(sec, terms, sec.basis[pick]), ref[pick], rtol=0, atol=1e-13)
+
+
+def test_diagonal_planted_mistake_is_caught(monkeypatch):
+    """A flipped sign of the Sz Sz term or a dropped 1/2 of the Hubbard term fails the pin."""
+    rng = np.random.default_rng(21)
+    sec2, sec4 = OracleSector(8, 2, 4, n_sub=2), OracleSector(5, 4, 6, n_sub=2)
+    t2, t4 = random_terms(rng, 8, 2, 8), random_terms(rng, 5, 4, 6)
+    ref2, ref4 = np.diag(restricted(sec2, t2)), np.diag(restricted(sec4, t4))
+    orig = oh._diag_term
+    monkeypatch.setattr(oh, "_diag_term", lambda s, k, i, j, c, w: orig(s, k, i, j, -c if k == "ZZ" else c, w))
+    assert not np.allclose(oh.diagonal(sec2, t2), ref2, atol=1e-10)
+    monkeypatch.setattr(oh, "_diag_term", lambda s, k, i, j, c, w: orig(s, k, i, j, 2 * c if k == "U" else c, w))
+    assert not np.allclose(oh.diagonal(sec4, t4), ref4, atol=1e-10)

@@ -61,3 +61,27 @@ def test_noalloc_rejects_too_large_and_off_path():
     t2 = b.make_terms(s2, wl.heisenberg_terms(wl.chain_bonds(12), 1.0))
     rc = lib.dq_matvec_noalloc(s2.handle, t2.handle, dummy, ctypes.c_void_p(0x10000000000), b.DQ_F64, _stream())
     assert rc == b.DQ_EINVAL
+
+
+def test_noalloc_call_takes_no_device_memory():
+    """After one call has done the per-device set-up, a call on a fresh sector and terms leaves the
+    device's free memory unchanged: the call itself allocates nothing."""
+    nn, nnn = wl.square_bonds(4, 4)
+    terms = wl.heisenberg_terms(nn, 1.0) + wl.heisenberg_terms(nnn, 0.5)
+    s0 = b.make_sector(16, 2, 8, 2)
+    t0 = b.make_terms(s0, terms)
+    x0 = torch.rand(s0.dim, dtype=torch.float64, device="cuda")
+    b.matvec_noalloc(s0, t0, x0, torch.empty_like(x0))  # set-up (and kernel load) on this device
+    s = b.make_sector(16, 2, 7, 2)
+    t = b.make_terms(s, terms)
+    assert t.path == "panel"
+    x = torch.rand(s.dim, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    ref = b.matvec(s, t, x, torch.empty_like(x))
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    b.matvec_noalloc(s, t, x, y)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.max(torch.abs(y - ref)).item() <= 1e-12 * torch.max(torch.abs(ref)).item()
