@@ -253,7 +253,7 @@ void dq_batch_free(dq_batch* b);
  * The workspace ((steps+1) vectors of D elements plus scratch) is allocated and freed by the
  * call, and the product's own scratch is kept with the terms (see dq_matvec).
  * Synchronous: returns when E0 (and psi) are known; one host synchronisation per step. Errors:
- * DQ_EINVAL (NULL or out-of-range arguments, steps > 4096 with reorth, a zero or non-finite v0),
+ * DQ_EINVAL (NULL or out-of-range arguments, steps outside [1, 4096], a zero or non-finite v0),
  * DQ_ENOMEM, DQ_ECUDA. */
 int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0, int steps, int dtype, int reorth,
                double* E0, double* alpha, double* beta, int* steps_done, void* psi, void* stream);

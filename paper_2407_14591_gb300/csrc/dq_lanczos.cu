@@ -401,7 +401,7 @@ extern "C" int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0,
     if (t->sector != s) return set_error(DQ_EINVAL, "terms were compiled for another sector");
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
     if (steps < 1) return set_error(DQ_EINVAL, "steps must be >= 1");
-    if (reorth && steps > 4096) return set_error(DQ_EINVAL, "steps must be <= 4096 with re-orthogonalisation");
+    if (steps > 4096) return set_error(DQ_EINVAL, "steps must be <= 4096");
     if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == DQ_F64)

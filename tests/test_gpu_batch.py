@@ -118,23 +118,27 @@ def test_workload4_largest_sectors_against_oracle_rows(workload4):
 
     ws, secs, terms, xs = workload4
     order = np.argsort([s.dim for s in secs])[::-1][:4]
+    outs = {}
     for dtype in (torch.float64, torch.float32):
         batch = b.make_batch(secs, terms, 8, dtype)
         xt = [torch.from_numpy(x).to(DEV, dtype) for x in xs]
         yt = [torch.empty_like(x) for x in xt]
         batch.matvec(xt, yt)
         torch.cuda.synchronize()
-        for k in order:
-            w, s = ws[k], secs[k]
-            o = OracleSector(w.L, 2, w.N, partition=s.partition)
-            rng = np.random.default_rng(int(k))
-            rows = np.unique(np.concatenate([np.arange(4096), rng.choice(s.dim, 1 << 16, replace=False),
-                                             np.arange(s.dim - 4096, s.dim)]))
-            xin = xt[k].double().cpu().numpy()
+        outs[dtype] = [(xt[k].double().cpu().numpy(), yt[k]) for k in order]
+        del batch
+    for q, k in enumerate(order):
+        w, s = ws[k], secs[k]
+        o = OracleSector(w.L, 2, w.N, partition=s.partition)
+        rng = np.random.default_rng(int(k))
+        rows = np.unique(np.concatenate([np.arange(4096), rng.choice(s.dim, 1 << 16, replace=False),
+                                         np.arange(s.dim - 4096, s.dim)]))
+        for dtype in (torch.float64, torch.float32):
+            xin, y = outs[dtype][q]
             ref = o_matvec_rows(o, w.terms, xin, rows)
-            got = yt[k][torch.from_numpy(rows).to(DEV)].double().cpu().numpy()
-            del o
+            got = y[torch.from_numpy(rows).to(DEV)].double().cpu().numpy()
             if dtype == torch.float64:
                 assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), (k, w.L, w.N)
             else:
                 assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), (k, w.L, w.N)
+        del o
