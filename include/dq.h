@@ -13,9 +13,13 @@
  *
  * Conventions shared by every call:
  *   - L sites, local dimension Q (2 <= Q <= 16), Nbits = ceil(log2 Q) bits per site, N particles
- *     (the paper's n). A basis state is one uint64 word; site i occupies bits
+ *     (the paper's n). A basis state is an integer word in which site i occupies bits
  *     [Nbits*(L-1-i), Nbits*(L-i)), i.e. site 0 is the most significant digit (Sec. 4.2).
- *     L * Nbits <= 64.
+ *     L * Nbits <= 128. With L * Nbits <= 64 a state is one uint64 and every function applies;
+ *     wider states (Sec. 4.1: the state class holds as many words as the sites need) take two
+ *     uint64 words, low word first (bits 0..63, then 64..127), and are read and written only by
+ *     the two-word forms (dq_state_at2, dq_index_of2, dq_next_state2, dq_state_at_batch2,
+ *     dq_index_of_batch2), which serve every sector.
  *   - The lattice is split into n_sub consecutive subsystems of most-equal length, the first
  *     (L mod n_sub) being one site longer (Sec. 4.3). n_sub = 0 selects the paper's default
  *     ceil(Nbits * L / 16) (Eq. (Nopt_from_L)).
@@ -82,7 +86,8 @@ const char* dq_last_error(void);
  * offset and stride tables (Eq. (offset), Eq. (stride)), one local rank table and one local
  * unrank list per distinct subsystem length (Sec. 4.2, container (i); filled with the
  * on-the-fly rank of Alg. 1), and their device copies on the current device.
- * Arguments: 1 <= L, L*Nbits <= 64, 2 <= Q <= 16, 0 <= N <= (Q-1)L, 0 <= n_sub <= L.
+ * Arguments: 1 <= L, L*Nbits <= 128, 2 <= Q <= 16, 0 <= N <= (Q-1)L, 0 <= n_sub <= L and
+ * n_sub <= 64.
  * Errors: DQ_EINVAL for out-of-range arguments; DQ_ERANGE if D >= 2^63 or a subsystem is wider
  * than 24 bits; DQ_ENOMEM / DQ_ECUDA on allocation failure. *out is set only on success and is
  * owned by the caller (dq_free_sector). Synchronous. */
@@ -99,25 +104,42 @@ int dq_sector_dim(const dq_sector* s, uint64_t* D);
 int dq_sector_partition(const dq_sector* s, int* n_sub, int* L_k);
 
 /* Function (iii), get_state (Sec. 2.2, Alg. 4), on the host: the state with canonical index
- * `index`. DQ_EINDEX if index >= D. */
+ * `index`. DQ_EINDEX if index >= D; DQ_EINVAL if the sector's states are wider than 64 bits
+ * (use dq_state_at2). */
 int dq_state_at(const dq_sector* s, uint64_t index, uint64_t* state);
 
 /* Function (i), get_index (Sec. 2.2, Alg. 2, Eq. (index)), on the host. DQ_ESTATE if `state`
- * has bits above L*Nbits, a digit >= Q, or a particle number other than N. */
+ * has bits above L*Nbits, a digit >= Q, or a particle number other than N. DQ_EINVAL if the
+ * sector's states are wider than 64 bits (use dq_index_of2). */
 int dq_index_of(const dq_sector* s, uint64_t state, uint64_t* index);
 
 /* Function (ii), increment (Sec. 2.2, Alg. 3), on the host: the next state in canonical order;
- * the last state wraps to the first (minimal) one. DQ_ESTATE for an invalid `state`. */
+ * the last state wraps to the first (minimal) one. DQ_ESTATE for an invalid `state`, DQ_EINVAL
+ * for a sector of states wider than 64 bits (use dq_next_state2). */
 int dq_next_state(const dq_sector* s, uint64_t state, uint64_t* next);
+
+/* Two-word forms of functions (iii), (i) and (ii) (same algorithms), for every sector: a state is
+ * the host array state[2] = {bits 0..63, bits 64..127}. Errors as the one-word forms. */
+int dq_state_at2(const dq_sector* s, uint64_t index, uint64_t* state);
+int dq_index_of2(const dq_sector* s, const uint64_t* state, uint64_t* index);
+int dq_next_state2(const dq_sector* s, const uint64_t* state, uint64_t* next);
 
 /* Batched function (iii) on the device: d_state[t] = get_state(d_index[t]) for t < n.
  * An index >= D writes UINT64_MAX and sets the sector's error word (see dq_check_device).
+ * DQ_EINVAL for a sector of states wider than 64 bits (use dq_state_at_batch2).
  * Asynchronous on `stream`. */
 int dq_state_at_batch(const dq_sector* s, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
 
 /* Batched function (i) on the device: d_index[t] = get_index(d_state[t]) for t < n.
- * An invalid state writes UINT64_MAX and sets the error word. Asynchronous on `stream`. */
+ * An invalid state writes UINT64_MAX and sets the error word. DQ_EINVAL for a sector of states
+ * wider than 64 bits (use dq_index_of_batch2). Asynchronous on `stream`. */
 int dq_index_of_batch(const dq_sector* s, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
+
+/* Two-word forms of the batches, for every sector: d_state holds 2 n uint64, state t at
+ * [2t, 2t+1] (low word first). An index >= D writes two UINT64_MAX words, an invalid state the
+ * index UINT64_MAX, and both raise the error word. Asynchronous on `stream`. */
+int dq_state_at_batch2(const dq_sector* s, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
+int dq_index_of_batch2(const dq_sector* s, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
 
 /* Synchronise `stream`, read and clear the sector's device error word. Returns DQ_EDEVICE if a
  * kernel flagged bad input since the last check, DQ_OK otherwise. */
@@ -127,7 +149,10 @@ int dq_check_device(const dq_sector* s, void* stream);
 
 /* Compile `n_terms` terms for sector `s` and upload them. Errors: DQ_EINVAL for an unknown kind,
  * a site out of range, i == j in a pair term, or a spin-1/2 kind with Q != 2. The same
- * (i, j) pair may appear in several terms; their contributions add. *out is owned by the caller
+ * (i, j) pair may appear in several terms; their contributions add. Q = 2 sectors of one-word
+ * states take the bond-layer form (pairs grouped by bit distance); other Q, and every sector of
+ * two-word states, take the per-term form (site functions, n_i n_j pairs, hops; the spin-1/2
+ * kinds rewritten as Sz = n - 1/2 and S+_i S-_j = b+_i b_j). *out is owned by the caller
  * (dq_free_terms). Synchronous. */
 int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_terms** out);
 
@@ -198,9 +223,9 @@ int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const void* x, void
  * in x or dy (Q = 2) gives NaN gradients and raises the sector's error word. The workspace
  * (2 * D * nrhs * 8 bytes for Q = 2, plus a few KB) is kept with the sector, grown on demand and
  * freed by dq_free_sector; calls on one sector from several host threads at once race on it.
- * Synchronous. Errors as dq_make_terms, plus DQ_EINVAL for bad dtype or nrhs, DQ_ENOMEM. The
- * paper's operator class (Sec. 4.1) has no derivatives; this serves training-style use of the
- * product. */
+ * Synchronous. Errors as dq_make_terms, plus DQ_EINVAL for bad dtype or nrhs or a sector of
+ * two-word states, DQ_ENOMEM. The paper's operator class (Sec. 4.1) has no derivatives; this
+ * serves training-style use of the product. */
 int dq_term_grads(const dq_sector* s, const dq_term* terms, int n_terms, const void* x, const void* dy, int dtype,
                   int nrhs, double* d_grads, void* stream);
 
@@ -214,7 +239,8 @@ typedef struct dq_batch dq_batch; /* opaque: up to 64 (sector, terms) pairs for 
  * in FP64 (the batched product is bound by its gathers of x, so the fixed-point prepass of
  * dq_matvec would only add traffic); FP32 vectors form products in FP32 and sum them with
  * compensated (Neumaier) summation. Errors: DQ_EINVAL (n, nrhs, dtype out of range; terms of
- * another sector; Q != 2), DQ_ENOMEM, DQ_ECUDA. *out is owned by the caller (dq_batch_free). */
+ * another sector; Q != 2 or two-word states), DQ_ENOMEM, DQ_ECUDA. *out is owned by the caller
+ * (dq_batch_free). */
 int dq_batch_make(int n, const dq_sector* const* sectors, const dq_terms* const* terms, int nrhs, int dtype,
                   dq_batch** out);
 
@@ -235,12 +261,12 @@ void dq_batch_free(dq_batch* b);
 
 /* Ground-state energy by Lanczos (Sec. 4.4, App. D): starting from v0 (device, D elements of
  * `dtype`, normalised inside the call, not modified), run up to `steps` steps of
- *   w = H v_k; alpha_k = <v_k, w>;
- *   reorth == 0: w -= alpha_k v_k + beta_{k-1} v_{k-1} (the plain three-term recurrence);
- *   reorth != 0: full re-orthogonalisation by classical Gram-Schmidt applied twice,
- *                w -= V (V^T w), w -= V (V^T w), V = [v_0 .. v_k]; the first pass's coefficient
- *                of v_k is alpha_k, and in exact arithmetic the first pass subtracts the same
- *                alpha_k v_k + beta_{k-1} v_{k-1} as the three-term step;
+ *   w = H v_k; alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1};
+ *   reorth == 1: full re-orthogonalisation by classical Gram-Schmidt against v_0 .. v_k,
+ *                w -= V (V^T w), repeated once more when that pass shrank ||w|| below 1/sqrt(2)
+ *                of its value before the pass (the Daniel-Gragg-Kaufman-Stewart criterion);
+ *   reorth == 2: the same with the second pass always;
+ *   reorth == 0: neither (the plain three-term recurrence);
  *   beta_k = ||w||; v_{k+1} = w / beta_k.
  * Dot products, norms and the vector updates are computed in FP64 whatever `dtype` is; the
  * Lanczos vectors are stored in `dtype`. E0 is the smallest eigenvalue of the tridiagonal matrix
@@ -250,11 +276,13 @@ void dq_batch_free(dq_batch* b);
  * psi (device, D elements of `dtype`, may be NULL) receives the Ritz vector of E0,
  * sum_k y_k v_k with y the unit eigenvector of T for E0 (inverse iteration on T, sign chosen so
  * that its largest component is positive); ||H psi - E0 psi|| is the residual of E0.
- * The workspace ((steps+1) vectors of D elements plus scratch) is allocated and freed by the
- * call, and the product's own scratch is kept with the terms (see dq_matvec).
- * Synchronous: returns when E0 (and psi) are known; one host synchronisation per step. Errors:
- * DQ_EINVAL (NULL or out-of-range arguments, steps outside [1, 4096], a zero or non-finite v0),
- * DQ_ENOMEM, DQ_ECUDA. */
+ * The workspace ((steps+1) vectors of D elements, scratch, 16 bytes of pinned host memory per
+ * step) is allocated and freed by the call, and the product's own scratch is kept with the terms
+ * (see dq_matvec). The steps run on `stream` without waiting for the host: the call reads each
+ * step's coefficients two steps later, so after a breakdown up to two more steps may have run;
+ * their results are dropped. Synchronous: returns when E0 (and psi) are known. Errors: DQ_EINVAL
+ * (NULL or out-of-range arguments, steps outside [1, 4096], reorth outside [0, 2], a zero or
+ * non-finite v0), DQ_ENOMEM, DQ_ECUDA (also for a non-finite coefficient). */
 int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0, int steps, int dtype, int reorth,
                double* E0, double* alpha, double* beta, int* steps_done, void* psi, void* stream);
 

@@ -55,8 +55,11 @@ def check_terms(sector: OracleSector, terms) -> list[tuple[str, int, int, float]
     return out
 
 
-def _bit(sector: OracleSector, i: int) -> np.uint64:
-    """Integer value of one particle on site i (lowest bit of its digit)."""
+def _bit(sector: OracleSector, i: int):
+    """Integer value of one particle on site i (lowest bit of its digit): np.uint64, or a Python
+    int for words wider than 64 bits."""
+    if sector.wide:
+        return 1 << (sector.nb * (sector.L - 1 - i))
     return np.uint64(1) << np.uint64(sector.nb * (sector.L - 1 - i))
 
 
@@ -80,7 +83,7 @@ def _diag_term(sector: OracleSector, kind: str, i: int, j: int, c: float, words)
 def diagonal(sector: OracleSector, terms, words=None) -> np.ndarray:
     """<sigma|H|sigma> for each word (default: the whole basis)."""
     terms = check_terms(sector, terms)
-    w = sector.basis if words is None else np.asarray(words, dtype=np.uint64)
+    w = sector.basis if words is None else sector.words_array(words)
     d = np.zeros(w.shape, dtype=np.float64)
     for kind, i, j, c in terms:
         if kind in ("ZZ", "Z", "NN", "N", "U"):

@@ -9,7 +9,9 @@ Conventions (written from the paper):
   sigma_i in {0..Q-1}; its particle number is the digit sum (Sec. 2.1, Eq. (nup)).
 * It is stored in one integer word with Nbits = ceil(log2 Q) bits per site, site 0 in the most
   significant digit (Sec. 4.2, the |3;2;1;0> -> 11100100 = 228 example). With this layout the
-  integer order of the words is the lexicographic order of the digit strings.
+  integer order of the words is the lexicographic order of the digit strings. Words of up to 64
+  bits are numpy uint64; wider words (L * Nbits up to 128; the paper's state class holds as many
+  words as the sites need, Sec. 4.1) are exact Python integers in object arrays (small sectors).
 * The lattice is split into n_sub consecutive subsystems P_0 .. P_{n_sub-1} (Sec. 3).
 * Canonical order (Sec. 3.1 and Sec. 3.2): P_{n_sub-1} varies fastest; each subsystem's states are
   ordered first by their own particle number n_k, then by a local order inside that sector. The
@@ -86,10 +88,16 @@ def _site_shift(L: int, nb: int, i: int) -> int:
     return nb * (L - 1 - i)
 
 
+def _int_of(words: np.ndarray, v: int):
+    """v as an operand for the word array: np.uint64 for uint64 words, a Python int for
+    exact-integer (object) words."""
+    return int(v) if words.dtype == object else np.uint64(v)
+
+
 def site_digit(words: np.ndarray, L: int, Q: int, i: int) -> np.ndarray:
     """Digit of site i for every word (vectorised)."""
     nb = nbits_for(Q)
-    return ((words >> np.uint64(_site_shift(L, nb, i))) & np.uint64((1 << nb) - 1)).astype(np.int64)
+    return ((words >> _int_of(words, _site_shift(L, nb, i))) & _int_of(words, (1 << nb) - 1)).astype(np.int64)
 
 
 def enumerate_lex(L: int, Q: int, N: int) -> np.ndarray:
@@ -101,16 +109,21 @@ def enumerate_lex(L: int, Q: int, N: int) -> np.ndarray:
     significant), ascending.
     """
     nb = nbits_for(Q)
-    if L * nb > 64:
-        raise ValueError("L * Nbits must be <= 64")
+    if L * nb > 128:
+        raise ValueError("L * Nbits must be <= 128")
+    wide = L * nb > 64
+    dt = object if wide else np.uint64
     if not 0 <= N <= (Q - 1) * L:
-        return np.zeros(0, dtype=np.uint64)
-    words = np.zeros(1, dtype=np.uint64)
+        return np.zeros(0, dtype=dt)
+    words = np.zeros(1, dtype=dt)
+    if wide:
+        words[0] = 0
     sums = np.zeros(1, dtype=np.int64)
-    digits = np.arange(Q, dtype=np.uint64)
+    digits = np.array([int(d) for d in range(Q)], dtype=object) if wide else np.arange(Q, dtype=np.uint64)
+    shift = int(nb) if wide else np.uint64(nb)
     for i in range(L):
         remaining = L - 1 - i
-        words = ((words[:, None] << np.uint64(nb)) | digits[None, :]).ravel()
+        words = ((words[:, None] << shift) | digits[None, :]).ravel()
         sums = (sums[:, None] + np.arange(Q, dtype=np.int64)[None, :]).ravel()
         keep = (sums <= N) & (sums + (Q - 1) * remaining >= N)
         words, sums = words[keep], sums[keep]
@@ -136,7 +149,7 @@ def subsystem_fields(words: np.ndarray, L: int, Q: int, part: list[int]):
     out = []
     for k, (s, Lk) in enumerate(zip(_subsystem_starts(part), part)):
         low_shift = nb * (L - s - Lk)
-        sig = (words >> np.uint64(low_shift)) & np.uint64((1 << (nb * Lk)) - 1)
+        sig = (words >> _int_of(words, low_shift)) & _int_of(words, (1 << (nb * Lk)) - 1)
         n_k = np.zeros(words.shape, dtype=np.int64)
         for i in range(s, s + Lk):
             n_k += site_digit(words, L, Q, i)
@@ -202,8 +215,8 @@ class OracleSector:
 
     def __init__(self, L: int, Q: int, N: int, n_sub: int = 0, partition: list[int] | None = None):
         nb = nbits_for(Q)
-        if L < 1 or L * nb > 64:
-            raise ValueError("need 1 <= L and L * Nbits <= 64")
+        if L < 1 or L * nb > 128:
+            raise ValueError("need 1 <= L and L * Nbits <= 128")
         if not 0 <= N <= (Q - 1) * L:
             raise ValueError("need 0 <= N <= (Q-1) L")
         self.L, self.Q, self.N, self.nb = L, Q, N, nb
@@ -228,15 +241,29 @@ class OracleSector:
 
     def digits(self, words: np.ndarray | None = None) -> np.ndarray:
         """(n, L) array of site digits (small sectors only)."""
-        w = self.basis if words is None else np.asarray(words, dtype=np.uint64)
+        w = self.basis if words is None else self.words_array(words)
         return np.stack([site_digit(w, self.L, self.Q, i) for i in range(self.L)], axis=1)
+
+    @property
+    def wide(self) -> bool:
+        """Words are wider than 64 bits (exact Python integers)."""
+        return self.L * self.nb > 64
+
+    def words_array(self, words) -> np.ndarray:
+        """Words as this sector stores them (uint64, or Python integers when wide)."""
+        if self.wide:
+            return np.array([int(v) for v in np.asarray(words, dtype=object).ravel()], dtype=object).reshape(
+                np.shape(words))
+        return np.asarray(words, dtype=np.uint64)
 
     def is_valid(self, words: np.ndarray) -> np.ndarray:
         """Word is a state of this sector: no bits above L*Nbits, digits < Q, digit sum N."""
-        w = np.asarray(words, dtype=np.uint64)
+        w = self.words_array(words)
         ok = np.ones(w.shape, dtype=bool)
         if self.L * self.nb < 64:
             ok &= (w >> np.uint64(self.L * self.nb)) == 0
+        elif self.wide:
+            ok &= (w >> (self.L * self.nb)) == 0
         tot = np.zeros(w.shape, dtype=np.int64)
         for i in range(self.L):
             d = site_digit(w, self.L, self.Q, i)
@@ -252,7 +279,7 @@ class OracleSector:
 
     def index_of_many(self, words: np.ndarray) -> np.ndarray:
         """Function (i) of Sec. 2.2 for many states: binary search of their keys."""
-        w = np.asarray(words, dtype=np.uint64)
+        w = self.words_array(words)
         if not np.all(self.is_valid(w)):
             raise ValueError("state not in this sector")
         k = composite_key(w, self.L, self.Q, self.partition)
@@ -261,7 +288,7 @@ class OracleSector:
         return pos.astype(np.int64)
 
     def index_of(self, word: int) -> int:
-        return int(self.index_of_many(np.array([word], dtype=np.uint64))[0])
+        return int(self.index_of_many(self.words_array([word]))[0])
 
     def next_state(self, word: int) -> int:
         """Function (ii) of Sec. 2.2: the next state in canonical order; the last wraps to the

@@ -27,6 +27,7 @@ KINDS = {"XY": 0, "ZZ": 1, "Z": 2, "HOP": 3, "NN": 4, "N": 5, "U": 6}
 EXPORTED = (
     "dq_last_error", "dq_make_sector", "dq_free_sector", "dq_sector_dim", "dq_sector_partition",
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
+    "dq_state_at2", "dq_index_of2", "dq_next_state2", "dq_state_at_batch2", "dq_index_of_batch2",
     "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_matvec_noalloc",
     "dq_lanczos", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free", "dq_term_grads",
     "dq_timing_enable", "dq_timing_read",
@@ -60,6 +61,11 @@ def _load() -> ctypes.CDLL:
         "dq_next_state": (i32, [vp, u64, P(u64)]),
         "dq_state_at_batch": (i32, [vp, vp, vp, u64, vp]),
         "dq_index_of_batch": (i32, [vp, vp, vp, u64, vp]),
+        "dq_state_at2": (i32, [vp, u64, P(u64)]),
+        "dq_index_of2": (i32, [vp, P(u64), P(u64)]),
+        "dq_next_state2": (i32, [vp, P(u64), P(u64)]),
+        "dq_state_at_batch2": (i32, [vp, vp, vp, u64, vp]),
+        "dq_index_of_batch2": (i32, [vp, vp, vp, u64, vp]),
         "dq_check_device": (i32, [vp, vp]),
         "dq_make_terms": (i32, [vp, P(_Term), i32, P(vp)]),
         "dq_free_terms": (None, [vp]),
@@ -129,20 +135,61 @@ class Sector:
             _lib.dq_free_sector(h)
             self._h = None
 
+    @property
+    def wide(self) -> bool:
+        """States take two words (L * Nbits > 64)."""
+        return self.L * (self.Q - 1).bit_length() > 64
+
     def state_at(self, index: int) -> int:
+        """Function (iii) on the host; the state as a Python int (two-word form when wide)."""
+        if self.wide:
+            out = (ctypes.c_uint64 * 2)()
+            _check(_lib.dq_state_at2(self._h, ctypes.c_uint64(index), out))
+            return int(out[0]) | (int(out[1]) << 64)
         out = ctypes.c_uint64()
         _check(_lib.dq_state_at(self._h, ctypes.c_uint64(index), ctypes.byref(out)))
         return int(out.value)
 
     def index_of(self, state: int) -> int:
         out = ctypes.c_uint64()
-        _check(_lib.dq_index_of(self._h, ctypes.c_uint64(state), ctypes.byref(out)))
+        if self.wide:
+            w = (ctypes.c_uint64 * 2)(state & (2 ** 64 - 1), state >> 64)
+            _check(_lib.dq_index_of2(self._h, w, ctypes.byref(out)))
+        else:
+            _check(_lib.dq_index_of(self._h, ctypes.c_uint64(state), ctypes.byref(out)))
         return int(out.value)
 
     def next_state(self, state: int) -> int:
+        if self.wide:
+            w = (ctypes.c_uint64 * 2)(state & (2 ** 64 - 1), state >> 64)
+            out = (ctypes.c_uint64 * 2)()
+            _check(_lib.dq_next_state2(self._h, w, out))
+            return int(out[0]) | (int(out[1]) << 64)
         out = ctypes.c_uint64()
         _check(_lib.dq_next_state(self._h, ctypes.c_uint64(state), ctypes.byref(out)))
         return int(out.value)
+
+    def state_at_batch2(self, index, out=None):
+        """Two-word batched function (iii): returns an int64 CUDA tensor of shape (n, 2), column 0
+        the low word and column 1 the high word of each state."""
+        import torch
+
+        idx = index.contiguous()
+        out = torch.empty((idx.numel(), 2), dtype=torch.int64, device=idx.device) if out is None else out
+        _check(_lib.dq_state_at_batch2(self._h, ctypes.c_void_p(idx.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       idx.numel(), _stream_handle()))
+        return out
+
+    def index_of_batch2(self, states, out=None):
+        """Two-word batched function (i): states is an int64 CUDA tensor of shape (n, 2)."""
+        import torch
+
+        st = states.contiguous()
+        n = st.shape[0]
+        out = torch.empty(n, dtype=torch.int64, device=st.device) if out is None else out
+        _check(_lib.dq_index_of_batch2(self._h, ctypes.c_void_p(st.data_ptr()), ctypes.c_void_p(out.data_ptr()), n,
+                                       _stream_handle()))
+        return out
 
     def state_at_batch(self, index, out=None):
         """Batched function (iii) on the device; index: int64/uint64 CUDA tensor."""
@@ -341,9 +388,11 @@ def make_batch(sectors, terms, nrhs: int, dtype) -> Batch:
     return Batch(sectors, terms, nrhs, dtype)
 
 
-def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True, want_vector: bool = False) -> dict:
-    """Ground-state energy by Lanczos (synchronous). Returns E0, alpha, beta, steps_done and, with
-    ``want_vector``, the Ritz vector of E0 as ``psi`` (a CUDA tensor like v0)."""
+def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth=True, want_vector: bool = False) -> dict:
+    """Ground-state energy by Lanczos (synchronous). ``reorth``: False/0 none, True/1 full
+    re-orthogonalisation (second Gram-Schmidt pass when needed), 2 (second pass always). Returns
+    E0, alpha, beta, steps_done and, with ``want_vector``, the Ritz vector of E0 as ``psi`` (a CUDA
+    tensor like v0)."""
     import torch
 
     _check_vec(sector, v0, "v0")
@@ -355,7 +404,7 @@ def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth: bool = True, w
     done = ctypes.c_int()
     psi = torch.empty_like(v0) if want_vector else None
     _check(_lib.dq_lanczos(sector.handle, terms.handle, ctypes.c_void_p(v0.data_ptr()), steps, _dtype_code(v0),
-                           1 if reorth else 0, ctypes.byref(E0), alpha, beta, ctypes.byref(done),
+                           int(reorth), ctypes.byref(E0), alpha, beta, ctypes.byref(done),
                            ctypes.c_void_p(psi.data_ptr() if psi is not None else 0), _stream_handle()))
     m = done.value
     out = {"E0": E0.value, "alpha": np.array(alpha[:m]), "beta": np.array(beta[:m]), "steps_done": m}

@@ -243,7 +243,7 @@ int dq_batch_make(int n, const dq_sector* const* sectors, const dq_terms* const*
         }
         if (!t->q2) {
             delete b;
-            return set_error(DQ_EINVAL, "item %d: the batched product serves Q = 2 sectors", k);
+            return set_error(DQ_EINVAL, "item %d: the batched product serves Q = 2 sectors of one-word states", k);
         }
         host[k].S = s->dev;
         host[k].H = t->q2v;

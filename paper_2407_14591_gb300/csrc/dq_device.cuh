@@ -18,8 +18,14 @@ __device__ __forceinline__ int digit_sum(uint32_t f, int nb) {
     }
 }
 
-__device__ __forceinline__ uint32_t field_of(const DevSector& S, uint64_t w, int k) {
-    return (uint32_t)((w >> S.shift[k]) & ((1ull << (S.nb * S.Lk[k])) - 1));
+// Word types of a basis state: one 64-bit word (L * Nbits <= 64) or a 128-bit pair of words
+// (64 < L * Nbits <= 128). The helpers below are templates over the word type; every shift
+// count is below the word's width.
+using u128 = unsigned __int128;
+
+template <typename W>
+__device__ __forceinline__ uint32_t field_of(const DevSector& S, W w, int k) {
+    return (uint32_t)(w >> S.shift[k]) & (uint32_t)((1ull << (S.nb * S.Lk[k])) - 1);
 }
 
 // Eq. (index) for a valid state. off_s / str_s may live in shared or global memory.
@@ -35,7 +41,8 @@ __device__ __forceinline__ uint64_t checked_rank(const DevSector& S, uint64_t j)
     return j;
 }
 
-__device__ __forceinline__ uint64_t d_rank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t w) {
+template <typename W>
+__device__ __forceinline__ uint64_t d_rank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, W w) {
     uint64_t idx = 0;
     int lam = 0;
     for (int k = 0; k < S.n_sub; ++k) {
@@ -50,9 +57,10 @@ __device__ __forceinline__ uint64_t d_rank(const DevSector& S, const uint64_t* o
 }
 
 // Lin's two-table form (Sec. 3.3): index = c_0(sigma^(0)) + index_1(sigma^(1)).
-__device__ __forceinline__ uint64_t d_rank_lin2(const DevSector& S, uint64_t w) {
+template <typename W>
+__device__ __forceinline__ uint64_t d_rank_lin2(const DevSector& S, W w) {
     uint32_t f0 = (uint32_t)(w >> S.shift[0]);
-    uint32_t f1 = (uint32_t)(w & ((1ull << (S.nb * S.Lk[1])) - 1));
+    uint32_t f1 = (uint32_t)w & (uint32_t)((1ull << (S.nb * S.Lk[1])) - 1);
     return checked_rank(S, __ldg(S.c0_tab + f0) + (uint64_t)__ldg(S.rank_tab[S.tab[1]] + f1));
 }
 
@@ -73,8 +81,9 @@ __device__ __forceinline__ uint64_t d_rank_within(const DevSector& S, const uint
 }
 
 // Alg. 4 for idx < D.
-__device__ __forceinline__ uint64_t d_unrank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t idx) {
-    uint64_t w = 0;
+template <typename W = uint64_t>
+__device__ __forceinline__ W d_unrank(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s, uint64_t idx) {
+    W w = 0;
     int lam = 0;
     for (int k = 0; k < S.n_sub; ++k) {
         int base = S.os_base[k] + lam * S.os_ld[k];
@@ -94,29 +103,34 @@ __device__ __forceinline__ uint64_t d_unrank(const DevSector& S, const uint64_t*
         }
         int t = S.tab[k];
         uint32_t pat = __ldg(S.unrank_tab[t] + __ldg(S.sec_start[t] + n) + li);
-        w |= (uint64_t)pat << S.shift[k];
+        w |= (W)pat << S.shift[k];
         lam += n;
     }
     return w;
 }
 
-__device__ __forceinline__ bool d_valid(const DevSector& S, uint64_t w) {
+__device__ __forceinline__ int popc_w(uint64_t v) { return __popcll(v); }
+__device__ __forceinline__ int popc_w(u128 v) { return __popcll((uint64_t)v) + __popcll((uint64_t)(v >> 64)); }
+
+template <typename W>
+__device__ __forceinline__ bool d_valid(const DevSector& S, W w) {
+    constexpr int WB = 8 * (int)sizeof(W);
     int bits = S.L * S.nb;
-    if (bits < 64 && (w >> bits) != 0) return false;
+    if (bits < WB && (w >> bits) != 0) return false;
     if ((S.Q & (S.Q - 1)) == 0) {
         // Q = 2^Nbits: every digit is < Q; the digit sum is a weighted popcount of bit planes
         int n = 0;
         for (int b = 0; b < S.nb; ++b) {
-            uint64_t plane = 0;
-            for (int q = b; q < 64; q += S.nb) plane |= 1ull << q;
-            n += __popcll(w & plane) << b;
+            W plane = 0;
+            for (int q = b; q < WB; q += S.nb) plane |= (W)1 << q;
+            n += popc_w(w & plane) << b;
         }
         return n == S.N;
     }
     int n = 0;
     unsigned m = (1u << S.nb) - 1;
     for (int i = 0; i < S.L; ++i) {
-        int d = (int)((w >> (S.nb * i)) & m);
+        int d = (int)((uint32_t)(w >> (S.nb * i)) & m);
         if (d >= S.Q) return false;
         n += d;
     }

@@ -237,6 +237,7 @@ extern "C" int dq_term_grads(const dq_sector* s, const dq_term* terms, int n_ter
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
     if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
     if (nrhs < 1 || nrhs > 64) return set_error(DQ_EINVAL, "nrhs must be in [1, 64]");
+    if (s->wide) return set_error(DQ_EINVAL, "dq_term_grads serves states of one 64-bit word (L * Nbits <= 64)");
     if (n_terms == 0) return DQ_OK;
     std::vector<GradTerm> gt(n_terms);
     for (int q = 0; q < n_terms; ++q) {

@@ -166,6 +166,7 @@ struct HostTables {
 
 struct dq_sector {
     int L, Q, N, nb, n_sub;
+    bool wide;  // L * Nbits > 64: states take two words (the 128-bit forms of every function)
     uint64_t D;
     int Lk[dq::kMaxSub], start[dq::kMaxSub];
     dq::HostTables h;
@@ -196,15 +197,20 @@ namespace dq {
 int set_error(int code, const char* fmt, ...);
 void clear_error();
 
-// host-side rank / unrank used by the ABI functions
-bool host_valid_state(const dq_sector* s, uint64_t w);
-uint64_t host_rank(const dq_sector* s, uint64_t w);
-uint64_t host_unrank(const dq_sector* s, uint64_t idx);
+// host-side rank / unrank used by the ABI functions, on 128-bit words (a one-word state is the
+// low word)
+using u128 = unsigned __int128;
+bool host_valid_state(const dq_sector* s, u128 w);
+uint64_t host_rank(const dq_sector* s, u128 w);
+u128 host_unrank(const dq_sector* s, uint64_t idx);
 
 // kernel launchers (dq_kernels.cu); return a cudaError_t as int
 int launch_state_at_batch(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
 int launch_index_of_batch(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
 int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
+// the same batches for states stored as two uint64 words (low word first)
+int launch_state_at_batch_w(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
+int launch_index_of_batch_w(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
 
 // panel product (dq_panel.cpp / dq_panel.cu)
 int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,

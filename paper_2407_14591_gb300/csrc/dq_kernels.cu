@@ -53,6 +53,43 @@ __global__ void k_index_of(DevSector S, const uint64_t* __restrict__ in, uint64_
     }
 }
 
+// The same two functions for states of two words (64 < L * Nbits <= 128, or any sector through
+// the two-word entry points): a state is stored as two uint64, the low word first.
+__global__ void k_state_at_w(DevSector S, const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n,
+                             bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t idx = in[t];
+        if (idx >= S.D) {
+            out[2 * t] = ~0ull;
+            out[2 * t + 1] = ~0ull;
+            atomicAdd(S.err, 1);
+        } else {
+            const u128 w = d_unrank<u128>(S, off_s, str_s, idx);
+            out[2 * t] = (uint64_t)w;
+            out[2 * t + 1] = (uint64_t)(w >> 64);
+        }
+    }
+}
+
+__global__ void k_index_of_w(DevSector S, const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n,
+                             bool use_sm) {
+    extern __shared__ uint64_t sm[];
+    const uint64_t *off_s, *str_s;
+    stage_os(S, sm, use_sm, off_s, str_s);
+    for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < n; t += (uint64_t)gridDim.x * blockDim.x) {
+        const u128 w = ((u128)in[2 * t + 1] << 64) | (u128)in[2 * t];
+        if (!d_valid(S, w)) {
+            out[t] = ~0ull;
+            atomicAdd(S.err, 1);
+        } else {
+            out[t] = d_rank(S, off_s, str_s, w);
+        }
+    }
+}
+
 constexpr int kMaxCh = 8;  // right-hand sides handled per pass
 
 // y = H x, Q = 2 operator, FP64 vectors in exact fixed point (row_q2_fx). CH: right-hand
@@ -83,7 +120,7 @@ __global__ void __launch_bounds__(256)
 // y = H x, general-Q operator (bosons), FP64 vectors in exact fixed point: digit functions and
 // n_i n_j pairs summed in int64, every allowed hop b+_a b_b a 128-bit multiply-add of its
 // amplitude -t sqrt((n_a + 1) n_b) (an integer on the grid 2^emin) with the gathered X.
-template <bool LIN2, int CH>
+template <typename W, bool LIN2, int CH>
 __global__ void __launch_bounds__(256)
     k_matvec_qg_fx(DevSector S, DevTermsQG H, const long long* __restrict__ X, double* __restrict__ y,
                    const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
@@ -101,13 +138,14 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin - hdr->F[col0 + c] : 0;
     const int Q = S.Q;
-    const uint64_t dm = (1ull << S.nb) - 1;
+    const uint32_t dm = (1u << S.nb) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step) {
-        const uint64_t s = d_unrank(S, off_s, str_s, i);
+        const W s = d_unrank<W>(S, off_s, str_s, i);
         long long md = H.MC;
-        for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite + q * Q + (int)((s >> H.site_sh[q]) & dm));
+        for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite + q * Q + (int)((uint32_t)(s >> H.site_sh[q]) & dm));
         for (int q = 0; q < H.npair; ++q) {
-            const int a = (int)((s >> H.pair_sh[2 * q]) & dm), b = (int)((s >> H.pair_sh[2 * q + 1]) & dm);
+            const int a = (int)((uint32_t)(s >> H.pair_sh[2 * q]) & dm);
+            const int b = (int)((uint32_t)(s >> H.pair_sh[2 * q + 1]) & dm);
             md += __ldg(H.Mpair + q) * (long long)(a * b);
         }
         I128 r[CH];
@@ -122,9 +160,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
                 const int s_up = dir ? sb : sa, s_dn = dir ? sa : sb;  // b+_up b_dn
-                const int nu = (int)((s >> s_up) & dm), nd = (int)((s >> s_dn) & dm);
+                const int nu = (int)((uint32_t)(s >> s_up) & dm), nd = (int)((uint32_t)(s >> s_dn) & dm);
                 if (nu < Q - 1 && nd > 0) {
-                    const uint64_t s2 = s + (1ull << s_up) - (1ull << s_dn);
+                    const W s2 = s + ((W)1 << s_up) - ((W)1 << s_dn);
                     const uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
                     const long long M = __ldg(H.Mhop + ((size_t)q * Q + nu) * Q + nd);
                     const long long* Xj = X + j * ld + col0;
@@ -167,7 +205,7 @@ __global__ void __launch_bounds__(256)
         row_q2_f32x<CH, LIN2>(S, H, off_s, str_s, wm, i, X, ld, col0, ch, sc, y);
 }
 
-template <bool LIN2, int CH>
+template <typename W, bool LIN2, int CH>
 __global__ void __launch_bounds__(256)
     k_matvec_qg_f32x(DevSector S, DevTermsQG H, const int* __restrict__ X, float* __restrict__ y,
                      const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
@@ -185,13 +223,14 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin32d - hdr->F[col0 + c] : 0;
     const int Q = S.Q;
-    const uint64_t dm = (1ull << S.nb) - 1;
+    const uint32_t dm = (1u << S.nb) - 1;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step) {
-        const uint64_t s = d_unrank(S, off_s, str_s, i);
+        const W s = d_unrank<W>(S, off_s, str_s, i);
         long long md = H.MC32;
-        for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite32 + q * Q + (int)((s >> H.site_sh[q]) & dm));
+        for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite32 + q * Q + (int)((uint32_t)(s >> H.site_sh[q]) & dm));
         for (int q = 0; q < H.npair; ++q) {
-            const int a = (int)((s >> H.pair_sh[2 * q]) & dm), b = (int)((s >> H.pair_sh[2 * q + 1]) & dm);
+            const int a = (int)((uint32_t)(s >> H.pair_sh[2 * q]) & dm);
+            const int b = (int)((uint32_t)(s >> H.pair_sh[2 * q + 1]) & dm);
             md += __ldg(H.Mpair32 + q) * (long long)(a * b);
         }
         long long hs[CH];
@@ -202,9 +241,9 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
             for (int dir = 0; dir < 2; ++dir) {
                 const int s_up = dir ? sb : sa, s_dn = dir ? sa : sb;  // b+_up b_dn
-                const int nu = (int)((s >> s_up) & dm), nd = (int)((s >> s_dn) & dm);
+                const int nu = (int)((uint32_t)(s >> s_up) & dm), nd = (int)((uint32_t)(s >> s_dn) & dm);
                 if (nu < Q - 1 && nd > 0) {
-                    const uint64_t s2 = s + (1ull << s_up) - (1ull << s_dn);
+                    const W s2 = s + ((W)1 << s_up) - ((W)1 << s_dn);
                     const uint64_t j = LIN2 ? d_rank_lin2(S, s2) : d_rank(S, off_s, str_s, s2);
                     const long long M = __ldg(H.Mhop32 + ((size_t)q * Q + nu) * Q + nd);
                     const int* Xj = X + j * ld + col0;
@@ -259,6 +298,18 @@ int launch_index_of_batch(const DevSector& S, const uint64_t* d_state, uint64_t*
     return (int)cudaGetLastError();
 }
 
+int launch_state_at_batch_w(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream) {
+    bool sm = os_in_smem(S);
+    k_state_at_w<<<grid_for(n, 256, 8), 256, sm ? os_bytes(S) : 0, (cudaStream_t)stream>>>(S, d_index, d_state, n, sm);
+    return (int)cudaGetLastError();
+}
+
+int launch_index_of_batch_w(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream) {
+    bool sm = os_in_smem(S);
+    k_index_of_w<<<grid_for(n, 256, 8), 256, sm ? os_bytes(S) : 0, (cudaStream_t)stream>>>(S, d_state, d_index, n, sm);
+    return (int)cudaGetLastError();
+}
+
 // FP64 vectors: column prepass into the terms' scratch, then the fixed-point kernel of the
 // operator's form (Q = 2 bond layers or general Q).
 static int launch_matvec_fx(const dq_sector* s, dq_terms* t, const double* x, double* y, int nrhs, cudaStream_t st) {
@@ -294,17 +345,22 @@ static int launch_matvec_fx(const dq_sector* s, dq_terms* t, const double* x, do
                 else
                     launch_resident(k_matvec_q2_fx<false, kMaxCh>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
             }
+        } else if (s->wide) {  // states of two words: Eq. (index) on 128-bit words
+            if (nrhs == 1)
+                launch_resident(k_matvec_qg_fx<u128, false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else
+                launch_resident(k_matvec_qg_fx<u128, false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
         } else {
             if (nrhs == 1) {
                 if (lin2)
-                    launch_resident(k_matvec_qg_fx<true, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<uint64_t, true, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
                 else
-                    launch_resident(k_matvec_qg_fx<false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<uint64_t, false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
             } else {
                 if (lin2)
-                    launch_resident(k_matvec_qg_fx<true, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<uint64_t, true, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
                 else
-                    launch_resident(k_matvec_qg_fx<false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+                    launch_resident(k_matvec_qg_fx<uint64_t, false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
             }
         }
     }
@@ -340,11 +396,14 @@ static int launch_matvec_f32x(const dq_sector* s, dq_terms* t, const float* x, f
             else if (one) launch_resident(k_matvec_q2_f32x<false, 1>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
             else if (lin2) launch_resident(k_matvec_q2_f32x<true, kMaxCh>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
             else launch_resident(k_matvec_q2_f32x<false, kMaxCh>, S.D, smb, st, S, t->q2v, X, y, h, nrhs, c0, ch, sm);
+        } else if (s->wide) {
+            if (one) launch_resident(k_matvec_qg_f32x<u128, false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else launch_resident(k_matvec_qg_f32x<u128, false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
         } else {
-            if (one && lin2) launch_resident(k_matvec_qg_f32x<true, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
-            else if (one) launch_resident(k_matvec_qg_f32x<false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
-            else if (lin2) launch_resident(k_matvec_qg_f32x<true, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
-            else launch_resident(k_matvec_qg_f32x<false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            if (one && lin2) launch_resident(k_matvec_qg_f32x<uint64_t, true, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else if (one) launch_resident(k_matvec_qg_f32x<uint64_t, false, 1>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else if (lin2) launch_resident(k_matvec_qg_f32x<uint64_t, true, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
+            else launch_resident(k_matvec_qg_f32x<uint64_t, false, kMaxCh>, S.D, smb, st, S, t->qgv, X, y, h, nrhs, c0, ch, sm);
         }
     }
     timing_stop(tslot, st, 2 + passes);

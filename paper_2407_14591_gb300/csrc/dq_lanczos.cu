@@ -1,17 +1,29 @@
 // Lanczos driver for the ground-state energy (Sec. 4.4; App. D calls a native Lanczos): the
 // only use of H is the matrix-free product. Vectors live on the device in the caller's dtype;
-// every dot product and norm accumulates in FP64 with a fixed reduction tree (the result does
-// not depend on timing). The tridiagonal matrix T is solved on the host by bisection on its
-// Sturm sequence, and the Ritz vector's coefficients by inverse iteration (own implementations).
+// every dot product, norm and vector update is computed in FP64 with a fixed reduction order (the
+// result does not depend on timing). The tridiagonal matrix T is solved on the host by bisection
+// on its Sturm sequence, and the Ritz vector's coefficients by inverse iteration (own
+// implementations).
 //
-// Data movement per step, with full re-orthogonalisation (classical Gram-Schmidt, twice):
-//   dots   h1 = V^T w            one pass over V, one pass over w per tile of kDotTile vectors
-//   update w -= V h1             one pass over V
-//   dots   h2 = V^T w            one pass over V
-//   update w -= V h2, ||w||^2    one pass over V
-//   scale  v_{k+1} = w / ||w||
-// The coefficients stay on the device (each kernel reads them from device memory); the host
-// reads alpha_k and ||w||^2 once per step, for T and for the breakdown test.
+// One step, all on the device:
+//   w = H v_k                                     (the product)
+//   alpha_k = <v_k, w>                            (k_gs_dots over one vector)
+//   w -= alpha_k v_k + beta_{k-1} v_{k-1}         (k_three_term, with rho0 = ||w||)
+//   with re-orthogonalisation, classical Gram-Schmidt against v_0 .. v_k:
+//     h = V^T w; w -= V h                         (k_gs_dots, k_gs_update, with rho1 = ||w||)
+//     a second pass only if rho1 < rho0 / sqrt(2) (the DGKS criterion; always with reorth = 2):
+//     the kernels of that pass read the decision from device memory and return at once when
+//     it is not needed
+//   beta_k = ||w||; v_{k+1} = w / beta_k           (k_normalise)
+// The reductions finish in the last block of each kernel (fixed order), the coefficients stay in
+// device memory, and each step copies alpha_k and beta_k^2 into pinned host memory. The host
+// reads step k's values only after it has queued step k+2 (two events in flight), so the GPU
+// never waits for the host; a breakdown found late only costs the steps already queued, whose
+// results are dropped.
+// Work per step: the product, one pass over v_k and v_{k-1}, and with re-orthogonalisation two
+// passes over V = [v_0 .. v_k] (dots, update), four when the second pass runs. The FP64 multiply-
+// adds of those passes (2 D (k+1)) are what bounds a step on this GPU, where FP64 runs at a small
+// fraction of the integer and FP32 rate.
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -25,12 +37,16 @@ namespace dq {
 constexpr int kRedThreads = 256;
 constexpr int kDotTile = 16;  // basis vectors per pass of the blocked dot kernel
 
-static int sm_count_now() {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms > 0 ? sms : 1;
-}
+// Device scalars of the driver (one array of doubles in the workspace).
+enum : int {
+    kAlpha = 0,    // alpha_k
+    kRho0 = 1,     // ||w||^2 after the three-term step
+    kRho1 = 2,     // ||w||^2 after the first Gram-Schmidt pass
+    kBeta2 = 3,    // ||w||^2 at the end of the step: beta_k^2
+    kPass2 = 4,    // 1.0 if the second pass runs
+    kV0 = 5,       // ||v0||^2
+    kNScal = 8,
+};
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -46,13 +62,39 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     return v;
 }
 
-// partial[j * gridDim.x + block] = sum over the block's rows of V_j[i] * w[i], for j < k.
-// The rows of a block are a grid stride; each pass takes kDotTile vectors at once, so w is read
-// once per tile instead of once per vector, and one block reduction serves the whole tile.
+// Called by every block after it wrote its partial result(s): returns true in the one block that
+// arrives last (which then sees every block's partials), and resets the counter for the next use.
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+        if (last) *counter = 0u;
+    }
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// Sum of partial[0 .. nb) in a fixed order (strided per thread, then the block tree).
+__device__ __forceinline__ double sum_partials(const double* partial, int nb, double* sh) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += __ldcg(partial + b);
+    return block_sum(acc, sh);
+}
+
+// out[j] = <V_j, w> for j < k, V_j = V + j * ldv. Each pass takes kDotTile vectors at once (w is
+// read once per tile) over the block's grid-stride rows; partial[b * k + j] holds block b's sums
+// and the last block adds them in block order. With `gate` (non-NULL) the kernel does nothing
+// unless *gate != 0.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_gs_dots(const T* __restrict__ V, size_t ldv, int k,
                                                           const T* __restrict__ w, uint64_t n,
-                                                          double* __restrict__ partial) {
+                                                          double* __restrict__ partial, double* __restrict__ out,
+                                                          unsigned* counter, const double* gate) {
+    if (gate && *gate == 0.0) return;
     __shared__ double sh[kDotTile][kRedThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
@@ -86,28 +128,29 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_dots(const T* __restrict__ V
         if (threadIdx.x < nj) {
             double s = 0.0;
             for (int r = 0; r < kRedThreads / 32; ++r) s += sh[threadIdx.x][r];
-            partial[(size_t)(j0 + threadIdx.x) * gridDim.x + blockIdx.x] = s;
+            partial[(size_t)blockIdx.x * k + j0 + threadIdx.x] = s;
         }
         __syncthreads();
     }
+    if (last_block(counter))
+        for (int j = threadIdx.x; j < k; j += blockDim.x) {
+            double s = 0.0;
+            for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (size_t)b * k + j);
+            out[j] = s;
+        }
 }
 
-// out[j] = sum_b partial[j * nb + b], one block per j.
-__global__ void k_finish(const double* __restrict__ partial, int nb, double* __restrict__ out) {
-    __shared__ double sh[32];
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += partial[(size_t)blockIdx.x * nb + b];
-    acc = block_sum(acc, sh);
-    if (threadIdx.x == 0) out[blockIdx.x] = acc;
-}
-
-// w[i] = w[i] - sum_{j<k} h[j] V_j[i] (FP64 arithmetic, stored in T); with NORM, also the
-// block's partial sum of the new w[i]^2 into norm_partial[block]. h is a device array of k
-// doubles, staged in shared memory.
-template <typename T, bool NORM>
+// w[i] -= sum_{j<k} h[j] V_j[i] (FP64 arithmetic, stored in T) and the new ||w||^2 into
+// scal[norm_slot]; the first pass (pass2 == false) also decides whether the second one runs
+// (scal[kPass2]: always with `always2`, else when the norm fell below 1/sqrt(2) of rho0), the
+// second (pass2 == true) does nothing unless scal[kPass2] is set. Both leave the step's final
+// ||w||^2 in scal[kBeta2].
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_gs_update(T* __restrict__ w, const T* __restrict__ V, size_t ldv,
                                                             int k, const double* __restrict__ h, uint64_t n,
-                                                            double* __restrict__ norm_partial) {
+                                                            double* __restrict__ partial, double* scal,
+                                                            unsigned* counter, bool pass2, bool always2) {
+    if (pass2 && scal[kPass2] == 0.0) return;
     extern __shared__ double hs[];
     __shared__ double red[32];
     for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
@@ -126,24 +169,31 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_update(T* __restrict__ w, co
         for (; j < k; ++j) acc -= hs[j] * (double)__ldg(V + (size_t)j * ldv + i);
         const T r = (T)acc;
         w[i] = r;
-        if (NORM) nacc += (double)r * (double)r;
+        nacc += (double)r * (double)r;
     }
-    if (NORM) {
-        nacc = block_sum(nacc, red);
-        if (threadIdx.x == 0) norm_partial[blockIdx.x] = nacc;
+    nacc = block_sum(nacc, red);
+    if (threadIdx.x == 0) partial[blockIdx.x] = nacc;
+    if (last_block(counter)) {
+        const double r2 = sum_partials(partial, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            if (!pass2) {
+                scal[kRho1] = r2;
+                scal[kPass2] = (always2 || r2 < 0.5 * scal[kRho0]) ? 1.0 : 0.0;
+            }
+            scal[kBeta2] = r2;
+        }
     }
 }
 
-// Plain three-term step without re-orthogonalisation: w -= alpha v + beta u (u may be NULL),
-// with alpha = *a and beta = sqrt(*bb) read from device memory, and the block's partial sum of
-// the new w^2.
+// w -= alpha v + beta u (u may be NULL; alpha = scal[kAlpha], beta^2 = beta2_prev), the new
+// ||w||^2 into scal[kRho0] and scal[kBeta2].
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_three_term(T* __restrict__ w, const T* __restrict__ v,
-                                                             const T* __restrict__ u, const double* __restrict__ a,
-                                                             const double* __restrict__ bb, uint64_t n,
-                                                             double* __restrict__ norm_partial) {
+                                                             const T* __restrict__ u, double* scal,
+                                                             const double* __restrict__ beta2_prev, uint64_t n,
+                                                             double* __restrict__ partial, unsigned* counter) {
     __shared__ double red[32];
-    const double al = *a, be = u ? sqrt(*bb) : 0.0;
+    const double al = scal[kAlpha], be = u ? sqrt(*beta2_prev) : 0.0;
     double nacc = 0.0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
         double acc = (double)w[i] - al * (double)v[i];
@@ -153,14 +203,22 @@ __global__ void __launch_bounds__(kRedThreads) k_three_term(T* __restrict__ w, c
         nacc += (double)r * (double)r;
     }
     nacc = block_sum(nacc, red);
-    if (threadIdx.x == 0) norm_partial[blockIdx.x] = nacc;
+    if (threadIdx.x == 0) partial[blockIdx.x] = nacc;
+    if (last_block(counter)) {
+        const double r2 = sum_partials(partial, gridDim.x, red);
+        if (threadIdx.x == 0) {
+            scal[kRho0] = r2;
+            scal[kBeta2] = r2;
+        }
+    }
 }
 
-// dst = src / sqrt(*nrm2) (the norm squared read from device memory).
+// dst = src / sqrt(*nrm2) (the norm squared read from device memory); a zero norm (an exact
+// invariant subspace) gives a zero vector.
 template <typename T>
 __global__ void k_normalise(T* __restrict__ dst, const T* __restrict__ src, const double* __restrict__ nrm2,
                             uint64_t n) {
-    const double s = 1.0 / sqrt(*nrm2);
+    const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
         dst[i] = (T)(s * (double)src[i]);
 }
@@ -273,7 +331,11 @@ static std::vector<double> tridiag_eigvec(const std::vector<double>& a, const st
 
 struct Work {
     std::vector<void*> allocs;
+    std::vector<void*> host_allocs;
+    std::vector<cudaEvent_t> events;
     ~Work() {
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        for (void* p : host_allocs) cudaFreeHost(p);
         for (void* p : allocs) cudaFree(p);
     }
     void* get(size_t bytes, int& rc) {
@@ -286,6 +348,16 @@ struct Work {
         allocs.push_back(p);
         return p;
     }
+    void* get_host(size_t bytes, int& rc) {
+        void* p = nullptr;
+        cudaError_t e = cudaMallocHost(&p, bytes);
+        if (e != cudaSuccess) {
+            rc = set_error(DQ_ENOMEM, "Lanczos cudaMallocHost(%zu): %s", bytes, cudaGetErrorString(e));
+            return nullptr;
+        }
+        host_allocs.push_back(p);
+        return p;
+    }
 };
 
 template <typename T>
@@ -293,8 +365,8 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
                        double* alpha_out, double* beta_out, int* steps_done, T* psi, cudaStream_t st) {
     const uint64_t D = s->D;
     const size_t ldv = (D + 31) & ~(size_t)31;
-    const int sms = sm_count_now();
-    const int nbd = 4 * sms;  // blocks of the dot kernels (one partial each)
+    const int sms = sm_count_cached();
+    const int nbd = 2 * sms;  // blocks of the dot kernel (one partial per vector each)
     const int nbu = 8 * sms;  // blocks of the streaming kernels
     int rc = DQ_OK;
     Work ws;
@@ -302,15 +374,27 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     if (!V) return rc;
     T* w = (T*)ws.get(ldv * sizeof(T), rc);
     if (!w) return rc;
-    const int nbmax = nbd > nbu ? nbd : nbu;
-    double* partial = (double*)ws.get((size_t)(steps + 2) * nbmax * sizeof(double), rc);
+    double* partial = (double*)ws.get((size_t)((steps + 1) * nbd + nbu) * sizeof(double), rc);
     if (!partial) return rc;
-    // device scalars: h1[0..steps], h2[0..steps], then [alpha, ||w||^2, ||v0||^2]
-    double* dres = (double*)ws.get((size_t)(2 * (steps + 1) + 8) * sizeof(double), rc);
-    if (!dres) return rc;
-    double* h1 = dres;
-    double* h2 = dres + (steps + 1);
-    double* dsc = dres + 2 * (steps + 1);
+    // device doubles: h[0 .. steps], then the scalars; counters of the last-block reductions
+    double* dd = (double*)ws.get((size_t)(steps + 1 + kNScal) * sizeof(double), rc);
+    if (!dd) return rc;
+    double* hv = dd;
+    double* scal = dd + (steps + 1);
+    unsigned* counter = (unsigned*)ws.get(4 * sizeof(unsigned), rc);
+    if (!counter) return rc;
+    double* beta2_prev = (double*)ws.get(sizeof(double), rc);  // beta_{k-1}^2 for the three-term step
+    if (!beta2_prev) return rc;
+    double* hst = (double*)ws.get_host((size_t)2 * steps * sizeof(double), rc);  // alpha_k, beta_k^2
+    if (!hst) return rc;
+    const int nev = 3;
+    for (int q = 0; q < nev; ++q) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return set_error(DQ_ECUDA, "Lanczos: cudaEventCreate failed");
+        ws.events.push_back(e);
+    }
+    cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned), st);
     const int dtype = sizeof(T) == 8 ? DQ_F64 : DQ_F32;
     auto cuda_fail = [&](const char* what) -> int {
         cudaError_t e = cudaGetLastError();
@@ -319,65 +403,77 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     };
 
     // v_0 = v0 / ||v0||
-    k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(v0, ldv, 1, v0, D, partial);
-    k_finish<<<1, kRedThreads, 0, st>>>(partial, nbd, dsc + 2);
+    k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(v0, ldv, 1, v0, D, partial, scal + kV0, counter, nullptr);
     double nrm2 = 0.0;
-    cudaError_t e = cudaMemcpyAsync(&nrm2, dsc + 2, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(&nrm2, scal + kV0, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos start vector: %s", cudaGetErrorString(e));
     if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) return set_error(DQ_EINVAL, "v0 has zero or non-finite norm");
-    k_normalise<T><<<nbu, kRedThreads, 0, st>>>(V, v0, dsc + 2, D);
+    k_normalise<T><<<nbu, kRedThreads, 0, st>>>(V, v0, scal + kV0, D);
+    cudaMemsetAsync(beta2_prev, 0, sizeof(double), st);
 
     std::vector<double> a, b;
-    double bprev = 0.0, tnorm = 0.0;
+    double tnorm = 0.0, bprev = 0.0;
     int m = 0;
+    bool stop = false;
+    // host side of step q: read its coefficients (its event has completed) and test for breakdown
+    auto consume = [&](int q) -> int {
+        cudaError_t ee = cudaEventSynchronize(ws.events[q % nev]);
+        if (ee != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos step: %s", cudaGetErrorString(ee));
+        if (stop) return DQ_OK;
+        const double al = hst[2 * q], be = std::sqrt(hst[2 * q + 1]);
+        a.push_back(al);
+        b.push_back(be);
+        m = q + 1;
+        tnorm = std::fmax(tnorm, std::fmax(std::fabs(al), std::fmax(be, bprev)));
+        bprev = be;
+        if (!std::isfinite(al) || !std::isfinite(be)) return set_error(DQ_ECUDA, "Lanczos: non-finite coefficient");
+        if (be < 1e-14 * tnorm) stop = true;
+        return DQ_OK;
+    };
+    int queued = 0;
     for (int k = 0; k < steps; ++k) {
+        if (k >= 2) {  // step k-2 done: the GPU still has step k-1 queued
+            if ((rc = consume(k - 2))) return rc;
+            if (stop) break;
+        }
         T* vk = V + (size_t)k * ldv;
         int le = launch_matvec(s, t, vk, w, dtype, 1, st);
         if (le) return set_error(DQ_ECUDA, "matvec launch: %s", cudaGetErrorString((cudaError_t)le));
+        k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(vk, ldv, 1, w, D, partial, scal + kAlpha, counter, nullptr);
+        k_three_term<T><<<nbu, kRedThreads, 0, st>>>(w, vk, k ? V + (size_t)(k - 1) * ldv : nullptr, scal,
+                                                    beta2_prev, D, partial, counter + 1);
         if (reorth) {
-            // h1 = V^T w (h1[k] = alpha_k), w -= V h1; h2 = V^T w, w -= V h2 with ||w||^2
             const int kk = k + 1;
             const size_t hsm = (size_t)kk * sizeof(double);
-            k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(V, ldv, kk, w, D, partial);
-            k_finish<<<kk, kRedThreads, 0, st>>>(partial, nbd, h1);
-            k_gs_update<T, false><<<nbu, kRedThreads, hsm, st>>>(w, V, ldv, kk, h1, D, nullptr);
-            k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(V, ldv, kk, w, D, partial);
-            k_finish<<<kk, kRedThreads, 0, st>>>(partial, nbd, h2);
-            k_gs_update<T, true><<<nbu, kRedThreads, hsm, st>>>(w, V, ldv, kk, h2, D, partial);
-            k_finish<<<1, kRedThreads, 0, st>>>(partial, nbu, dsc + 1);
-            cudaMemcpyAsync(dsc, h1 + k, sizeof(double), cudaMemcpyDeviceToDevice, st);
-        } else {
-            // alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1} with ||w||^2
-            k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(vk, ldv, 1, w, D, partial);
-            k_finish<<<1, kRedThreads, 0, st>>>(partial, nbd, dsc);
-            // dsc[1] still holds ||w_{k-1}||^2 = beta_{k-1}^2 when k > 0
-            k_three_term<T><<<nbu, kRedThreads, 0, st>>>(w, vk, k ? V + (size_t)(k - 1) * ldv : nullptr, dsc, dsc + 1,
-                                                        D, partial);
-            k_finish<<<1, kRedThreads, 0, st>>>(partial, nbu, dsc + 1);
+            for (int pass = 0; pass < 2; ++pass) {
+                k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(V, ldv, kk, w, D, partial, hv, counter + 2,
+                                                         pass ? scal + kPass2 : nullptr);
+                k_gs_update<T><<<nbu, kRedThreads, hsm, st>>>(w, V, ldv, kk, hv, D, partial + (size_t)kk * nbd, scal,
+                                                             counter + 3, pass == 1, reorth == 2);
+            }
         }
-        if (k + 1 < steps) k_normalise<T><<<nbu, kRedThreads, 0, st>>>(V + (size_t)(k + 1) * ldv, w, dsc + 1, D);
+        if (k + 1 < steps) k_normalise<T><<<nbu, kRedThreads, 0, st>>>(V + (size_t)(k + 1) * ldv, w, scal + kBeta2, D);
+        cudaMemcpyAsync(beta2_prev, scal + kBeta2, sizeof(double), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(hst + 2 * k, scal + kAlpha, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(hst + 2 * k + 1, scal + kBeta2, sizeof(double), cudaMemcpyDeviceToHost, st);
+        cudaEventRecord(ws.events[k % nev], st);
         if ((rc = cuda_fail("step"))) return rc;
-        double hs2[2];
-        e = cudaMemcpyAsync(hs2, dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, st);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos step: %s", cudaGetErrorString(e));
-        const double al = hs2[0], be = std::sqrt(hs2[1]);
-        a.push_back(al);
-        b.push_back(be);
-        m = k + 1;
-        tnorm = std::fmax(tnorm, std::fmax(std::fabs(al), std::fmax(be, bprev)));
-        if (k == steps - 1 || be < 1e-14 * tnorm) break;
-        bprev = be;
+        queued = k + 1;
     }
+    for (int q = (queued >= 2 ? queued - 2 : 0); q < queued && !stop; ++q) {
+        if (q < m) continue;
+        if ((rc = consume(q))) return rc;
+    }
+    if (m == 0) return set_error(DQ_ECUDA, "Lanczos: no step completed");
     std::vector<double> off(b.begin(), b.begin() + (m - 1));
     const double e0 = m == 1 ? a[0] : tridiag_min_eig(a, off);
     *E0 = e0;
     if (psi) {
         std::vector<double> y = m == 1 ? std::vector<double>{1.0} : tridiag_eigvec(a, off, e0);
-        e = cudaMemcpyAsync(h1, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, st);
+        e = cudaMemcpyAsync(hv, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos Ritz vector: %s", cudaGetErrorString(e));
-        k_combination<T><<<nbu, kRedThreads, (size_t)m * sizeof(double), st>>>(psi, V, ldv, m, h1, D);
+        k_combination<T><<<nbu, kRedThreads, (size_t)m * sizeof(double), st>>>(psi, V, ldv, m, hv, D);
         if ((rc = cuda_fail("Ritz vector"))) return rc;
     }
     e = cudaStreamSynchronize(st);
@@ -400,8 +496,8 @@ extern "C" int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0,
     if (!s || !t || !v0 || !E0) return set_error(DQ_EINVAL, "NULL argument");
     if (t->sector != s) return set_error(DQ_EINVAL, "terms were compiled for another sector");
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
-    if (steps < 1) return set_error(DQ_EINVAL, "steps must be >= 1");
-    if (steps > 4096) return set_error(DQ_EINVAL, "steps must be <= 4096");
+    if (steps < 1 || steps > 4096) return set_error(DQ_EINVAL, "steps must be in [1, 4096]");
+    if (reorth < 0 || reorth > 2) return set_error(DQ_EINVAL, "reorth must be 0, 1 or 2");
     if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
     cudaStream_t st = (cudaStream_t)stream;
     if (dtype == DQ_F64)

@@ -131,12 +131,13 @@ static inline uint64_t Dq(const dq_sector* s, int l, long m) {
     return s->h.Dq[(size_t)l * s->h.dq_ld + (size_t)m];
 }
 
-static inline int digit(const dq_sector* s, uint64_t w, int site) {
-    return (int)((w >> (s->nb * (s->L - 1 - site))) & ((1u << s->nb) - 1));
+// States are handled as 128-bit words on the host; a one-word state is the low word.
+static inline int digit(const dq_sector* s, u128 w, int site) {
+    return (int)((uint32_t)(w >> (s->nb * (s->L - 1 - site))) & ((1u << s->nb) - 1));
 }
 
-static inline uint32_t field(const dq_sector* s, uint64_t w, int k) {
-    return (uint32_t)((w >> s->dev.shift[k]) & ((1ull << (s->nb * s->Lk[k])) - 1));
+static inline uint32_t field(const dq_sector* s, u128 w, int k) {
+    return (uint32_t)(w >> s->dev.shift[k]) & (uint32_t)((1ull << (s->nb * s->Lk[k])) - 1);
 }
 
 static int pattern_n(int nb, uint32_t pat, int len) {
@@ -145,9 +146,9 @@ static int pattern_n(int nb, uint32_t pat, int len) {
     return n;
 }
 
-bool host_valid_state(const dq_sector* s, uint64_t w) {
+bool host_valid_state(const dq_sector* s, u128 w) {
     int bits = s->L * s->nb;
-    if (bits < 64 && (w >> bits) != 0) return false;
+    if (bits < 128 && (w >> bits) != 0) return false;
     int n = 0;
     for (int i = 0; i < s->L; ++i) {
         int d = digit(s, w, i);
@@ -158,7 +159,7 @@ bool host_valid_state(const dq_sector* s, uint64_t w) {
 }
 
 // Alg. 2 (function (i), get_index): index = sum_k offset_k(n_k, lambda_k) + stride_k * index_k.
-uint64_t host_rank(const dq_sector* s, uint64_t w) {
+uint64_t host_rank(const dq_sector* s, u128 w) {
     uint64_t idx = 0;
     int lam = 0;
     for (int k = 0; k < s->n_sub; ++k) {
@@ -175,8 +176,8 @@ uint64_t host_rank(const dq_sector* s, uint64_t w) {
 
 // Alg. 4 (function (iii), get_state): per subsystem, the particle number is the n with
 // offset(n) <= idx < offset(n+1); the local index is the quotient by the stride.
-uint64_t host_unrank(const dq_sector* s, uint64_t idx) {
-    uint64_t w = 0;
+u128 host_unrank(const dq_sector* s, uint64_t idx) {
+    u128 w = 0;
     int lam = 0;
     for (int k = 0; k < s->n_sub; ++k) {
         int t = s->dev.tab[k];
@@ -192,7 +193,7 @@ uint64_t host_unrank(const dq_sector* s, uint64_t idx) {
         uint64_t li = (k == s->n_sub - 1) ? rem : rem / st;
         idx = rem - li * st;
         uint32_t pat = s->h.unrank_tab[t][s->h.sec_start[t][n] + li];
-        w |= (uint64_t)pat << s->dev.shift[k];
+        w |= (u128)pat << s->dev.shift[k];
         lam += n;
     }
     return w;
@@ -200,18 +201,18 @@ uint64_t host_unrank(const dq_sector* s, uint64_t idx) {
 
 // Minimal state of `len` sites holding n particles: particles as far right as possible
 // (index 0 of the canonical order, App. B get_minimal_state). Returned right-aligned.
-static uint64_t minimal_state(int nb, int Q, int len, int n) {
-    uint64_t w = 0;
+static u128 minimal_state(int nb, int Q, int len, int n) {
+    u128 w = 0;
     for (int i = 0; i < len && n > 0; ++i) {  // i counts sites from the right end
         int d = n < Q - 1 ? n : Q - 1;
-        w |= (uint64_t)d << (nb * i);
+        w |= (u128)d << (nb * i);
         n -= d;
     }
     return w;
 }
 
 // Alg. 3 (function (ii), increment).
-static uint64_t host_increment(const dq_sector* s, uint64_t w) {
+static u128 host_increment(const dq_sector* s, u128 w) {
     int lam = 0;    // particles in the suffix after P_k
     int gamma = 0;  // sites in that suffix
     for (int j = 1; j <= s->n_sub; ++j) {
@@ -221,12 +222,13 @@ static uint64_t host_increment(const dq_sector* s, uint64_t w) {
         int n = pattern_n(s->nb, f, s->Lk[k]);
         uint64_t li = s->h.rank_tab[t][f];
         uint64_t dim_local = Dq(s, s->Lk[k], n);
-        uint64_t keep_mask = (s->dev.shift[k] + s->nb * s->Lk[k] >= 64) ? 0 : (~0ull << (s->dev.shift[k] + s->nb * s->Lk[k]));
+        const int top = s->dev.shift[k] + s->nb * s->Lk[k];
+        const u128 keep_mask = top >= 128 ? (u128)0 : (~(u128)0 << top);
         if (li + 1 < dim_local) {
             uint32_t nxt = s->h.unrank_tab[t][s->h.sec_start[t][n] + li + 1];
-            return (w & keep_mask) | ((uint64_t)nxt << s->dev.shift[k]) | minimal_state(s->nb, s->Q, gamma, lam);
+            return (w & keep_mask) | ((u128)nxt << s->dev.shift[k]) | minimal_state(s->nb, s->Q, gamma, lam);
         } else if (lam > 0 && n < (s->Q - 1) * s->Lk[k]) {
-            uint64_t pk = minimal_state(s->nb, s->Q, s->Lk[k], n + 1);
+            u128 pk = minimal_state(s->nb, s->Q, s->Lk[k], n + 1);
             return (w & keep_mask) | (pk << s->dev.shift[k]) | minimal_state(s->nb, s->Q, gamma, lam - 1);
         }
         gamma += s->Lk[k];
@@ -265,7 +267,7 @@ static int build(dq_sector* s) {
         pos += s->Lk[k];
         v.Lk[k] = s->Lk[k];
         v.shift[k] = nb * (L - pos);
-        for (int b = v.shift[k]; b < v.shift[k] + nb * s->Lk[k]; ++b) v.sub_of[b] = (signed char)k;
+        for (int b = v.shift[k]; b < v.shift[k] + nb * s->Lk[k] && b < 64; ++b) v.sub_of[b] = (signed char)k;
         v.nmax[k] = (Q - 1) * s->Lk[k];
         int t = -1;
         for (int q = 0; q < ntab; ++q)
@@ -402,14 +404,16 @@ int dq_make_sector(int L, int Q, int N, int n_sub, dq_sector** out) {
     if (Q < 2 || Q > 16) return set_error(DQ_EINVAL, "Q must be in [2, 16]");
     int nb = 0;
     while ((1 << nb) < Q) ++nb;
-    if (L < 1 || L * nb > 64) return set_error(DQ_EINVAL, "need 1 <= L and L * Nbits <= 64");
+    if (L < 1 || L * nb > 128) return set_error(DQ_EINVAL, "need 1 <= L and L * Nbits <= 128");
     if (N < 0 || N > (Q - 1) * L) return set_error(DQ_EINVAL, "need 0 <= N <= (Q-1) L");
     if (n_sub < 0 || n_sub > L) return set_error(DQ_EINVAL, "need 0 <= n_sub <= L");
     if (n_sub == 0) n_sub = (nb * L + 15) / 16;  // Eq. (Nopt_from_L)
     if (n_sub < 1) n_sub = 1;
+    if (n_sub > kMaxSub) return set_error(DQ_EINVAL, "at most %d subsystems", kMaxSub);
     dq_sector* s = new (std::nothrow) dq_sector();
     if (!s) return set_error(DQ_ENOMEM, "host allocation");
     s->L = L; s->Q = Q; s->N = N; s->nb = nb; s->n_sub = n_sub;
+    s->wide = L * nb > 64;
     int base = L / n_sub, extra = L % n_sub;  // most-equal, longer parts first (Sec. 4.3)
     for (int k = 0; k < n_sub; ++k) s->Lk[k] = base + (k < extra ? 1 : 0);
     s->device = 0;
@@ -454,18 +458,27 @@ int dq_sector_partition(const dq_sector* s, int* n_sub, int* L_k) {
     return DQ_OK;
 }
 
+static int narrow_only(const dq_sector* s, const char* fn) {
+    if (s->wide)
+        return set_error(DQ_EINVAL, "%s: the sector's states are %d bits wide; use the two-word form %s2", fn,
+                         s->L * s->nb, fn);
+    return DQ_OK;
+}
+
 int dq_state_at(const dq_sector* s, uint64_t index, uint64_t* state) {
     clear_error();
     if (!s || !state) return set_error(DQ_EINVAL, "NULL argument");
+    if (int rc = narrow_only(s, "dq_state_at")) return rc;
     if (index >= s->D) return set_error(DQ_EINDEX, "index %llu >= D = %llu", (unsigned long long)index,
                                         (unsigned long long)s->D);
-    *state = host_unrank(s, index);
+    *state = (uint64_t)host_unrank(s, index);
     return DQ_OK;
 }
 
 int dq_index_of(const dq_sector* s, uint64_t state, uint64_t* index) {
     clear_error();
     if (!s || !index) return set_error(DQ_EINVAL, "NULL argument");
+    if (int rc = narrow_only(s, "dq_index_of")) return rc;
     if (!host_valid_state(s, state)) return set_error(DQ_ESTATE, "word 0x%llx is not a state of the sector",
                                                       (unsigned long long)state);
     *index = host_rank(s, state);
@@ -475,15 +488,54 @@ int dq_index_of(const dq_sector* s, uint64_t state, uint64_t* index) {
 int dq_next_state(const dq_sector* s, uint64_t state, uint64_t* next) {
     clear_error();
     if (!s || !next) return set_error(DQ_EINVAL, "NULL argument");
+    if (int rc = narrow_only(s, "dq_next_state")) return rc;
     if (!host_valid_state(s, state)) return set_error(DQ_ESTATE, "word 0x%llx is not a state of the sector",
                                                       (unsigned long long)state);
-    *next = host_increment(s, state);
+    *next = (uint64_t)host_increment(s, state);
+    return DQ_OK;
+}
+
+static inline u128 from_words(const uint64_t* w) { return ((u128)w[1] << 64) | (u128)w[0]; }
+static inline void to_words(u128 v, uint64_t* w) {
+    w[0] = (uint64_t)v;
+    w[1] = (uint64_t)(v >> 64);
+}
+
+int dq_state_at2(const dq_sector* s, uint64_t index, uint64_t* state) {
+    clear_error();
+    if (!s || !state) return set_error(DQ_EINVAL, "NULL argument");
+    if (index >= s->D) return set_error(DQ_EINDEX, "index %llu >= D = %llu", (unsigned long long)index,
+                                        (unsigned long long)s->D);
+    to_words(host_unrank(s, index), state);
+    return DQ_OK;
+}
+
+int dq_index_of2(const dq_sector* s, const uint64_t* state, uint64_t* index) {
+    clear_error();
+    if (!s || !state || !index) return set_error(DQ_EINVAL, "NULL argument");
+    const u128 w = from_words(state);
+    if (!host_valid_state(s, w))
+        return set_error(DQ_ESTATE, "word 0x%016llx%016llx is not a state of the sector", (unsigned long long)state[1],
+                         (unsigned long long)state[0]);
+    *index = host_rank(s, w);
+    return DQ_OK;
+}
+
+int dq_next_state2(const dq_sector* s, const uint64_t* state, uint64_t* next) {
+    clear_error();
+    if (!s || !state || !next) return set_error(DQ_EINVAL, "NULL argument");
+    const u128 w = from_words(state);
+    if (!host_valid_state(s, w))
+        return set_error(DQ_ESTATE, "word 0x%016llx%016llx is not a state of the sector", (unsigned long long)state[1],
+                         (unsigned long long)state[0]);
+    to_words(host_increment(s, w), next);
     return DQ_OK;
 }
 
 int dq_state_at_batch(const dq_sector* s, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream) {
     clear_error();
     if (!s || (n && (!d_index || !d_state))) return set_error(DQ_EINVAL, "NULL argument");
+    if (int rc = narrow_only(s, "dq_state_at_batch")) return rc;
     if (n == 0) return DQ_OK;
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
     int e = launch_state_at_batch(s->dev, d_index, d_state, n, stream);
@@ -494,10 +546,31 @@ int dq_state_at_batch(const dq_sector* s, const uint64_t* d_index, uint64_t* d_s
 int dq_index_of_batch(const dq_sector* s, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream) {
     clear_error();
     if (!s || (n && (!d_index || !d_state))) return set_error(DQ_EINVAL, "NULL argument");
+    if (int rc = narrow_only(s, "dq_index_of_batch")) return rc;
     if (n == 0) return DQ_OK;
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
     int e = launch_index_of_batch(s->dev, d_state, d_index, n, stream);
     if (e) return set_error(DQ_ECUDA, "index_of_batch launch: %s", cudaGetErrorString((cudaError_t)e));
+    return DQ_OK;
+}
+
+int dq_state_at_batch2(const dq_sector* s, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream) {
+    clear_error();
+    if (!s || (n && (!d_index || !d_state))) return set_error(DQ_EINVAL, "NULL argument");
+    if (n == 0) return DQ_OK;
+    if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
+    int e = launch_state_at_batch_w(s->dev, d_index, d_state, n, stream);
+    if (e) return set_error(DQ_ECUDA, "state_at_batch2 launch: %s", cudaGetErrorString((cudaError_t)e));
+    return DQ_OK;
+}
+
+int dq_index_of_batch2(const dq_sector* s, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream) {
+    clear_error();
+    if (!s || (n && (!d_index || !d_state))) return set_error(DQ_EINVAL, "NULL argument");
+    if (n == 0) return DQ_OK;
+    if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
+    int e = launch_index_of_batch_w(s->dev, d_state, d_index, n, stream);
+    if (e) return set_error(DQ_ECUDA, "index_of_batch2 launch: %s", cudaGetErrorString((cudaError_t)e));
     return DQ_OK;
 }
 

@@ -284,9 +284,31 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     std::map<std::pair<int, int>, double> nn;
     std::vector<int> hop_sh;
     std::vector<double> hop_t;
+    double C = 0.0;  // constant part of the diagonal
     for (int q = 0; q < n; ++q) {
         const dq_term& u = terms[q];
         switch (u.kind) {
+            // spin-1/2 kinds in this form (Q = 2, used for states of two words): Sz = n - 1/2,
+            //   Z:  c Sz_i               = c n_i - c/2
+            //   ZZ: c Sz_i Sz_j          = c n_i n_j - c/2 n_i - c/2 n_j + c/4
+            //   XY: c/2 (S+_i S-_j + h.c.) = a hop with amplitude c/2, i.e. t = -c/2
+            case DQ_Z:
+                for (int d = 0; d < Q; ++d) f[u.i][d] += u.coef * d;
+                C += -0.5 * u.coef;
+                break;
+            case DQ_ZZ:
+                nn[{u.i < u.j ? u.i : u.j, u.i < u.j ? u.j : u.i}] += u.coef;
+                for (int d = 0; d < Q; ++d) {
+                    f[u.i][d] += -0.5 * u.coef * d;
+                    f[u.j][d] += -0.5 * u.coef * d;
+                }
+                C += 0.25 * u.coef;
+                break;
+            case DQ_XY:
+                hop_sh.push_back(nb * (L - 1 - u.i));
+                hop_sh.push_back(nb * (L - 1 - u.j));
+                hop_t.push_back(-0.5 * u.coef);
+                break;
             case DQ_N:
                 for (int d = 0; d < Q; ++d) f[u.i][d] += u.coef * d;
                 break;
@@ -299,7 +321,7 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
                 hop_sh.push_back(nb * (L - 1 - u.j));
                 hop_t.push_back(u.coef);
                 break;
-            default: return set_error(DQ_EINVAL, "spin-1/2 term kinds need Q = 2");
+            default: return set_error(DQ_EINVAL, "unknown term kind %d", u.kind);
         }
     }
     DevTermsQG& v = t->qgv;
@@ -345,7 +367,7 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         for (int q = 0; q < v.nhop; ++q)
             for (int a = 0; a < Q - 1; ++a)
                 for (int b = 1; b < Q; ++b) hop_amp[((size_t)q * Q + a) * Q + b] = -hop_t[q] * amp[(size_t)a * Q + b];
-        double cmax = 0.0;
+        double cmax = std::fabs(C);
         for (double u : site_f) cmax = std::max(cmax, std::fabs(u));
         for (double u : pair_K) cmax = std::max(cmax, std::fabs(u));
         for (double u : hop_amp) cmax = std::max(cmax, std::fabs(u));
@@ -355,7 +377,7 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         const int mbits = std::min(55, 62 - lg);
         v.emin = cmax > 0.0 ? std::ilogb(cmax) + 1 - mbits : 0;
         auto M = [&](double c) { return (long long)std::llrint(std::ldexp(c, -v.emin)); };
-        v.MC = 0;
+        v.MC = M(C);
         auto upm = [&](const std::vector<double>& src, const long long** dst) -> int {
             std::vector<long long> m(src.size());
             for (size_t k = 0; k < src.size(); ++k) m[k] = M(src[k]);
@@ -369,13 +391,13 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         if ((rc = upm(hop_amp, &v.Mhop))) return rc;
         // FP32 vectors: hop amplitudes with at most 24 bits (int32), the diagonal on a finer grid
         {
-            double cmax_h = 0.0, cmax_d = 0.0;
+            double cmax_h = 0.0, cmax_d = std::fabs(C);
             for (double u : hop_amp) cmax_h = std::max(cmax_h, std::fabs(u));
             for (double u : site_f) cmax_d = std::max(cmax_d, std::fabs(u));
             for (double u : pair_K) cmax_d = std::max(cmax_d, std::fabs(u));
             fp32_grids(cmax_h, cmax_d, tdiag, 2 * v.nhop, &v.emin32, &v.emin32d);
         }
-        v.MC32 = 0;
+        v.MC32 = (long long)std::llrint(std::ldexp(C, -v.emin32d));
         auto upd = [&](const std::vector<double>& src, const long long** dst) -> int {
             std::vector<long long> m(src.size());
             for (size_t k = 0; k < src.size(); ++k) m[k] = (long long)std::llrint(std::ldexp(src[k], -v.emin32d));
@@ -418,7 +440,9 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
     dq_terms* t = new (std::nothrow) dq_terms();
     if (!t) return set_error(DQ_ENOMEM, "host allocation");
     t->sector = s;
-    t->q2 = (s->Q == 2);
+    // Q = 2 takes the bond-layer form (64-bit words only); general Q, and every sector whose
+    // states take two words, the per-term form
+    t->q2 = (s->Q == 2) && !s->wide;
     int rc;
     try {
         rc = t->q2 ? compile_q2(s, terms, n_terms, t) : compile_qg(s, terms, n_terms, t);

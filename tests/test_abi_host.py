@@ -42,7 +42,8 @@ def test_library_exports_every_declared_symbol():
 
 CASES = [(9, 2, 4, 3), (10, 2, 5, 2), (12, 2, 6, 5), (11, 2, 4, 11), (8, 3, 7, 3), (7, 4, 9, 2), (9, 3, 5, 4),
          (6, 5, 10, 3), (5, 16, 20, 2), (12, 2, 0, 3), (12, 2, 12, 2), (11, 4, 11, 2), (16, 2, 8, 1), (13, 3, 11, 0),
-         (64, 2, 2, 4), (64, 2, 3, 3), (32, 4, 3, 3)]
+         (64, 2, 2, 4), (64, 2, 3, 3), (32, 4, 3, 3),
+         (70, 2, 2, 5), (33, 4, 3, 3), (128, 2, 2, 8), (100, 2, 2, 0), (42, 8, 2, 0)]  # two-word states
 
 
 @pytest.mark.parametrize("L,Q,N,n_sub", CASES)
@@ -76,8 +77,8 @@ def test_workload_dimensions():
 
 
 def test_argument_errors():
-    for args in [(0, 2, 0, 1), (10, 1, 3, 1), (10, 17, 3, 1), (65, 2, 3, 4), (33, 4, 3, 3), (10, 2, 11, 2),
-                 (10, 2, -1, 2), (10, 2, 5, 11), (10, 2, 5, -1)]:
+    for args in [(0, 2, 0, 1), (10, 1, 3, 1), (10, 17, 3, 1), (129, 2, 3, 9), (65, 4, 3, 5), (10, 2, 11, 2),
+                 (10, 2, -1, 2), (10, 2, 5, 11), (10, 2, 5, -1), (128, 2, 2, 65)]:
         with pytest.raises(b.DQError) as e:
             b.make_sector(*args)
         assert e.value.code == b.DQ_EINVAL
@@ -131,3 +132,27 @@ def test_timing_hooks_without_products():
     assert b.timing_read() == (0.0, 0, 0)
     b.timing_enable(False)
     assert b.timing_read() == (0.0, 0, 0)
+
+
+def test_two_word_forms():
+    """States wider than 64 bits: the one-word functions refuse the sector (DQ_EINVAL) and the
+    two-word ones serve it; on a one-word sector the two-word forms equal the one-word ones."""
+    lib = b.lib()
+    w = b.make_sector(70, 2, 2, 5)
+    out = ctypes.c_uint64()
+    assert lib.dq_state_at(w.handle, ctypes.c_uint64(0), ctypes.byref(out)) == b.DQ_EINVAL
+    assert b"two-word" in lib.dq_last_error()
+    assert lib.dq_index_of(w.handle, ctypes.c_uint64(3), ctypes.byref(out)) == b.DQ_EINVAL
+    assert lib.dq_state_at_batch(w.handle, ctypes.c_void_p(16), ctypes.c_void_p(32), 1, None) == b.DQ_EINVAL
+    top = (1 << 69) | (1 << 68)  # both particles on the first two sites: the last state
+    assert w.index_of(top) == w.dim - 1 and w.state_at(w.dim - 1) == top
+    assert w.next_state(top) == w.state_at(0) == 0b11
+    with pytest.raises(b.DQError) as e:
+        w.index_of((1 << 70) | 1)
+    assert e.value.code == b.DQ_ESTATE
+    n = b.make_sector(20, 2, 10, 2)
+    st2 = (ctypes.c_uint64 * 2)()
+    for i in (0, 17, n.dim - 1):
+        assert lib.dq_state_at2(n.handle, ctypes.c_uint64(i), st2) == b.DQ_OK
+        assert st2[1] == 0 and st2[0] == n.state_at(i)
+        assert lib.dq_index_of2(n.handle, st2, ctypes.byref(out)) == b.DQ_OK and out.value == i

@@ -275,3 +275,43 @@ def test_diagonal_planted_mistake_is_caught(monkeypatch):
     assert not np.allclose(oh.diagonal(sec2, t2), ref2, atol=1e-10)
     monkeypatch.setattr(oh, "_diag_term", lambda s, k, i, j, c, w: orig(s, k, i, j, 2 * c if k == "U" else c, w))
     assert not np.allclose(oh.diagonal(sec4, t4), ref4, atol=1e-10)
+
+
+@pytest.mark.parametrize("Lw,L,Q,N", [(66, 12, 2, 3), (70, 10, 2, 2), (33, 7, 4, 3)])
+def test_wide_words_embedding_equals_narrow_oracle(Lw, L, Q, N):
+    """Terms on the first L sites of an Lw-site lattice (words wider than 64 bits): the states
+    with every particle on those sites form an invariant block, and on it the wide product equals
+    the one-word product of the L-site lattice (itself pinned to the Kronecker construction),
+    word w mapping to w << Nbits (Lw - L); x supported on the block gives y zero elsewhere."""
+    rng = np.random.default_rng(Lw + L + Q)
+    terms = random_terms(rng, L, Q, L + 2)
+    narrow = OracleSector(L, Q, N, n_sub=2)
+    wide = OracleSector(Lw, Q, N, n_sub=0)
+    assert wide.wide and not narrow.wide
+    nb = (Q - 1).bit_length()
+    shift = nb * (Lw - L)
+    rows = wide.index_of_many(wide.words_array([int(w) << shift for w in narrow.basis]))
+    x = rng.uniform(-1, 1, narrow.dim)
+    xw = np.zeros(wide.dim)
+    xw[rows] = x
+    yw = matvec(wide, terms, xw)
+    np.testing.assert_allclose(yw[rows], matvec(narrow, terms, x), rtol=0, atol=1e-13)
+    rest = np.ones(wide.dim, dtype=bool)
+    rest[rows] = False
+    assert np.all(yw[rest] == 0.0)
+    np.testing.assert_allclose(matvec_rows(wide, terms, xw, rows[:50]), yw[rows[:50]], rtol=0, atol=1e-13)
+
+
+def test_wide_words_free_fermion_e0():
+    """A disordered periodic XX chain of 66 sites with 2 particles (66-bit words): the oracle
+    Lanczos E0 equals the Jordan-Wigner free-fermion value."""
+    L, N = 66, 2
+    rng = np.random.default_rng(66)
+    bonds = wl.chain_bonds(L, True)
+    J = rng.uniform(0.5, 1.5, len(bonds))
+    h = rng.uniform(-1, 1, L)
+    terms = wl.heisenberg_terms(bonds, J, 0.0) + wl.field_terms(h)
+    sec = OracleSector(L, 2, N, n_sub=5)
+    assert sec.wide
+    res = lanczos(lambda v: matvec(sec, terms, v), rng.uniform(-1, 1, sec.dim), 100)
+    assert res["E0"] == pytest.approx(free_fermion_e0(L, N, J, h, True), abs=1e-10)

@@ -294,3 +294,60 @@ def test_full_width_words_sort_by_the_key_tuple(L, Q, N, part):
     assert all(sum(digits(w)) == N for w in words[:50])
     idx = np.arange(0, o.dim, max(1, o.dim // 500))
     assert np.array_equal(o.index_of_many(o.basis[idx]), idx)
+
+
+# ---------------------------------------------------------------- words wider than 64 bits ---
+
+def _q2_words_brute(L, N):
+    from itertools import combinations
+    return sorted(sum(1 << (L - 1 - i) for i in c) for c in combinations(range(L), N))
+
+
+def _q4_words_brute(L, N):
+    """All digit strings over {0..3} with digit sum N <= 3 (N particles placed on sites with
+    repetition), as Python integers, sorted."""
+    from itertools import combinations_with_replacement
+    return sorted({sum(1 << (2 * (L - 1 - i)) for i in c) for c in combinations_with_replacement(range(L), N)})
+
+
+@pytest.mark.parametrize("L,Q,N", [(70, 2, 2), (100, 2, 3), (128, 2, 2), (33, 4, 3), (64, 4, 2)])
+def test_wide_words_enumeration_matches_brute_force(L, Q, N):
+    """Words of more than 64 bits are exact integers; lexicographic enumeration equals the sorted
+    brute-force list of all digit strings with digit sum N, and the dimension is Eq. (dim)'s."""
+    words = [int(w) for w in enumerate_lex(L, Q, N)]
+    ref = _q2_words_brute(L, N) if Q == 2 else _q4_words_brute(L, N)
+    assert words == ref
+    assert len(words) == sector_dim(L, Q, N) == dim_closed_form(L, Q, N)
+
+
+@pytest.mark.parametrize("L,Q,N,n_sub", [(70, 2, 2, 3), (66, 2, 2, 5), (33, 4, 3, 3), (128, 2, 2, 8)])
+def test_wide_words_order_matches_offset_stride_recipe(L, Q, N, n_sub):
+    """The canonical order of two-word states equals Eq. (index) written out in this test (on
+    every state, or every 5th for the largest case), and rank(unrank(i)) = i through the binary
+    search."""
+    sec = OracleSector(L, Q, N, n_sub=n_sub)
+    assert sec.wide
+    pick = range(0, sec.dim, 5 if sec.dim > 5000 else 1)
+    got = [recipe_index(int(sec.basis[r]), L, Q, N, sec.partition) for r in pick]
+    assert got == list(pick)
+    idx = np.arange(0, sec.dim, max(1, sec.dim // 300))
+    assert np.array_equal(sec.index_of_many(sec.basis[idx]), idx)
+    assert sec.next_state(int(sec.basis[-1])) == int(sec.basis[0])
+
+
+def test_wide_words_cover_index_over_subsystem_letters():
+    """Sec. 3.4 on a sector of 66-bit words: Cover's index over the letters (n_k, sigma^(k)) is
+    the canonical index (checked on a sample of states)."""
+    sec = OracleSector(66, 2, 2, partition=[22, 22, 22])
+    S = _key_tuples(sec)
+    for r in list(range(0, sec.dim, 97)) + [sec.dim - 1]:
+        assert cover_index(S[r], S) == r
+
+
+def test_wide_words_validity():
+    sec = OracleSector(70, 2, 2, n_sub=3)
+    good = (1 << 69) | 1
+    assert sec.is_valid([good]).all()
+    assert not sec.is_valid([(1 << 70) | 1]).any()  # a bit above L * Nbits
+    assert not sec.is_valid([(1 << 69) | 3]).any()  # three particles
+    assert sec.state_at(sec.index_of(good)) == good
