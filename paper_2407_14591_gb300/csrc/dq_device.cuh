@@ -109,6 +109,57 @@ __device__ __forceinline__ W d_unrank(const DevSector& S, const uint64_t* off_s,
     return w;
 }
 
+// Walk of one lane over the rows i, i + 32, i + 64, ... of a warp (the lanes take consecutive
+// rows, so loads and stores stay coalesced). The first row is unranked with Alg. 4. The last
+// subsystem has offset 0 and stride 1 in Eq. (index), so consecutive indices run through its
+// particle-number sector in its local order: while the last subsystem's local index plus 32 stays
+// inside that sector, the next row differs from this one only in the last subsystem's pattern,
+// read from the unrank list (Alg. 3 applied 32 times at once); otherwise Alg. 4 again.
+template <typename W>
+struct RowWalk {
+    W s;                   // the row's word
+    uint32_t li, len;      // local index of the last subsystem, size of its sector
+    const uint32_t* list;  // unrank list of that sector
+};
+
+template <typename W>
+__device__ __forceinline__ void walk_start(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s,
+                                           uint64_t idx, RowWalk<W>& r) {
+    W w = 0;
+    int lam = 0;
+    const int last = S.n_sub - 1;
+    for (int k = 0; k < last; ++k) {
+        const int base = S.os_base[k] + lam * S.os_ld[k];
+        int n = 0;
+        while (n < S.nmax[k] && !(idx < off_s[base + n + 1])) ++n;
+        idx -= off_s[base + n];
+        const uint64_t st = str_s[base + n];
+        const uint64_t li = idx / st;
+        idx -= li * st;
+        const int t = S.tab[k];
+        w |= (W)__ldg(S.unrank_tab[t] + __ldg(S.sec_start[t] + n) + li) << S.shift[k];
+        lam += n;
+    }
+    const int t = S.tab[last], n = S.N - lam;
+    const uint32_t s0 = __ldg(S.sec_start[t] + n);
+    r.list = S.unrank_tab[t] + s0;
+    r.len = __ldg(S.sec_start[t] + n + 1) - s0;
+    r.li = (uint32_t)idx;
+    r.s = w | (W)__ldg(r.list + r.li);  // the last subsystem sits at shift 0
+}
+
+template <typename W>
+__device__ __forceinline__ void walk_next(const DevSector& S, const uint64_t* off_s, const uint64_t* str_s,
+                                          uint64_t idx, RowWalk<W>& r) {
+    if (r.li + 32 < r.len) {
+        r.li += 32;
+        const W lowmask = ((W)1 << (S.nb * S.Lk[S.n_sub - 1])) - 1;
+        r.s = (r.s & ~lowmask) | (W)__ldg(r.list + r.li);
+    } else {
+        walk_start(S, off_s, str_s, idx, r);
+    }
+}
+
 __device__ __forceinline__ int popc_w(uint64_t v) { return __popcll(v); }
 __device__ __forceinline__ int popc_w(u128 v) { return __popcll((uint64_t)v) + __popcll((uint64_t)(v >> 64)); }
 

@@ -92,12 +92,33 @@ __global__ void k_index_of_w(DevSector S, const uint64_t* __restrict__ in, uint6
 
 constexpr int kMaxCh = 8;  // right-hand sides handled per pass
 
+// Row loop of the product kernels: each warp takes chunks of 32 R consecutive rows, lane l the
+// rows base + l + 32 r (r < R), walked with walk_start / walk_next (one Alg. 4 unrank per chunk
+// and lane, then mostly a read of the last subsystem's unrank list). The body sees the row index
+// i and the walk rw (rw.s is the row's word).
+#define WARP_ROWS_BEGIN(W)                                                                             \
+    const uint64_t wid_ = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;                      \
+    const uint64_t nwarp_ = ((uint64_t)gridDim.x * blockDim.x) >> 5;                                   \
+    const uint64_t span_ = 32ull * (uint64_t)R;                                                        \
+    for (uint64_t base_ = wid_ * span_; base_ < S.D; base_ += nwarp_ * span_) {                        \
+        RowWalk<W> rw;                                                                                 \
+        uint64_t i = base_ + (threadIdx.x & 31);                                                       \
+        for (int r_ = 0; r_ < R && i < S.D; ++r_, i += 32) {                                           \
+            if (r_ == 0)                                                                               \
+                walk_start(S, off_s, str_s, i, rw);                                                    \
+            else                                                                                       \
+                walk_next(S, off_s, str_s, i, rw);
+#define WARP_ROWS_END \
+        }             \
+    }
+
+
 // y = H x, Q = 2 operator, FP64 vectors in exact fixed point (row_q2_fx). CH: right-hand
 // sides per pass (1, or kMaxCh for nrhs > 1).
 template <bool LIN2, int CH>
 __global__ void __launch_bounds__(256)
     k_matvec_q2_fx(DevSector S, DevTermsQ2 H, const long long* __restrict__ X, double* __restrict__ y,
-                   const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
+                   const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm, int R) {
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
@@ -113,8 +134,9 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin - hdr->F[col0 + c] : 0;
     __shared__ uint64_t wm[kMaxLayers];
     stage_within(S, H, wm);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
-        row_q2_fx<CH, LIN2>(S, H, off_s, str_s, wm, i, X, ld, col0, ch, sc, y);
+    WARP_ROWS_BEGIN(uint64_t)
+        row_q2_fx<CH, LIN2>(S, H, off_s, str_s, wm, i, rw.s, X, ld, col0, ch, sc, y);
+    WARP_ROWS_END
 }
 
 // y = H x, general-Q operator (bosons), FP64 vectors in exact fixed point: digit functions and
@@ -123,7 +145,7 @@ __global__ void __launch_bounds__(256)
 template <typename W, bool LIN2, int CH>
 __global__ void __launch_bounds__(256)
     k_matvec_qg_fx(DevSector S, DevTermsQG H, const long long* __restrict__ X, double* __restrict__ y,
-                   const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
+                   const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm, int R) {
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
@@ -139,8 +161,8 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin - hdr->F[col0 + c] : 0;
     const int Q = S.Q;
     const uint32_t dm = (1u << S.nb) - 1;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step) {
-        const W s = d_unrank<W>(S, off_s, str_s, i);
+    WARP_ROWS_BEGIN(W)
+        const W s = rw.s;
         long long md = H.MC;
         for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite + q * Q + (int)((uint32_t)(s >> H.site_sh[q]) & dm));
         for (int q = 0; q < H.npair; ++q) {
@@ -176,7 +198,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int c = 0; c < CH; ++c)
             if (c < ch) yi[c] = i128_to<double>(r[c], sc[c]);
-    }
+    WARP_ROWS_END
 }
 
 // y = H x for FP32 vectors in fixed point (int32 X, int32 hop amplitudes, int64 hop sums, the
@@ -185,7 +207,7 @@ __global__ void __launch_bounds__(256)
 template <bool LIN2, int CH>
 __global__ void __launch_bounds__(256)
     k_matvec_q2_f32x(DevSector S, DevTermsQ2 H, const int* __restrict__ X, float* __restrict__ y,
-                     const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
+                     const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm, int R) {
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
@@ -201,14 +223,15 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin32d - hdr->F[col0 + c] : 0;
     __shared__ uint64_t wm[kMaxLayers];
     stage_within(S, H, wm);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step)
-        row_q2_f32x<CH, LIN2>(S, H, off_s, str_s, wm, i, X, ld, col0, ch, sc, y);
+    WARP_ROWS_BEGIN(uint64_t)
+        row_q2_f32x<CH, LIN2>(S, H, off_s, str_s, wm, i, rw.s, X, ld, col0, ch, sc, y);
+    WARP_ROWS_END
 }
 
 template <typename W, bool LIN2, int CH>
 __global__ void __launch_bounds__(256)
     k_matvec_qg_f32x(DevSector S, DevTermsQG H, const int* __restrict__ X, float* __restrict__ y,
-                     const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm) {
+                     const ColScale* __restrict__ hdr, int ld, int col0, int ch, bool use_sm, int R) {
     extern __shared__ uint64_t sm[];
     const uint64_t *off_s, *str_s;
     stage_os(S, sm, use_sm, off_s, str_s);
@@ -224,8 +247,8 @@ __global__ void __launch_bounds__(256)
     for (int c = 0; c < CH; ++c) sc[c] = c < ch ? H.emin32d - hdr->F[col0 + c] : 0;
     const int Q = S.Q;
     const uint32_t dm = (1u << S.nb) - 1;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < S.D; i += step) {
-        const W s = d_unrank<W>(S, off_s, str_s, i);
+    WARP_ROWS_BEGIN(W)
+        const W s = rw.s;
         long long md = H.MC32;
         for (int q = 0; q < H.nsite; ++q) md += __ldg(H.Msite32 + q * Q + (int)((uint32_t)(s >> H.site_sh[q]) & dm));
         for (int q = 0; q < H.npair; ++q) {
@@ -263,7 +286,7 @@ __global__ void __launch_bounds__(256)
             add_i64_shl(r, hs[c], H.emin32 - H.emin32d);
             yi[c] = i128_to<float>(r, sc[c]);
         }
-    }
+    WARP_ROWS_END
 }
 
 static int num_sms() { return sm_count_cached(); }
@@ -280,10 +303,16 @@ static unsigned grid_for(uint64_t n, int threads, int per_sm) {
 // Launches a grid-stride product kernel with 256 threads on as many blocks as can be resident at
 // once (the occupancy calculator for this kernel's registers and this launch's dynamic shared
 // memory, cached per kernel and size), capped by the row count: one wave, no tail of late blocks.
+// The last kernel argument is R, the rows per lane of a warp's chunk (WARP_ROWS_BEGIN): as many
+// as keep at least four chunks per warp, at most 16.
 template <typename... KArgs, typename... Args>
 static void launch_resident(void (*kernel)(KArgs...), uint64_t rows, size_t smb, cudaStream_t st, Args... args) {
     const int per_sm = occupancy_cached(reinterpret_cast<const void*>(kernel), 256, smb);
-    kernel<<<grid_for(rows, 256, per_sm), 256, smb, st>>>(args...);
+    const unsigned grid = grid_for(rows, 256, per_sm);
+    const uint64_t lanes = (uint64_t)grid * 256;
+    uint64_t R = rows / (lanes * 4);
+    R = R < 1 ? 1 : (R > 16 ? 16 : R);
+    kernel<<<grid, 256, smb, st>>>(args..., (int)R);
 }
 
 int launch_state_at_batch(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream) {

@@ -52,16 +52,15 @@ __device__ __forceinline__ void for_each_hop(const DevSector& S, const uint64_t*
     }
 }
 
-// Row i of y = H x: X holds x as int64 (row-major, ld values per row, columns col0 .. col0+ch-1
+// Row i (word s) of y = H x: X holds x as int64 (row-major, ld values per row, columns col0 .. col0+ch-1
 // used), the coefficients are integers times 2^emin (DevTermsQ2), sc[c] = emin - F of column
 // col0 + c. The diagonal is an int64 sum; every row result is a 128-bit sum rounded once.
 // Layers with one hop amplitude add their gathered X in int64 and multiply once.
 template <int CH, bool LIN2>
 __device__ __forceinline__ void row_q2_fx(const DevSector& S, const DevTermsQ2& H, const uint64_t* off_s,
-                                          const uint64_t* str_s, const uint64_t* wm, uint64_t i,
+                                          const uint64_t* str_s, const uint64_t* wm, uint64_t i, uint64_t s,
                                           const long long* __restrict__ X, int ld, int col0, int ch, const int* sc,
                                           double* __restrict__ y) {
-    const uint64_t s = d_unrank(S, off_s, str_s, i);
     long long md = H.MC;
     if (H.Mlin) {
         uint64_t m = s;
@@ -135,7 +134,7 @@ __device__ __forceinline__ void add_i64_shl(I128& a, long long v, int sh) {
     a.lo = lo;
 }
 
-// Row i of y = H x for FP32 vectors in fixed point: X holds x as int32 (|X| < 2^30); hop
+// Row i (word s) of y = H x for FP32 vectors in fixed point: X holds x as int32 (|X| < 2^30); hop
 // amplitudes are int32 multiples of 2^emin32 (|m| < 2^24, fewer bits for rows with very many
 // hops), so every hop is one 32x32 -> 64-bit product added to an int64 row sum (the host keeps
 // max_hops * 2^(bits + 30) below 2^62); diagonal coefficients are int64 multiples of the finer
@@ -143,10 +142,9 @@ __device__ __forceinline__ void add_i64_shl(I128& a, long long v, int sh) {
 // once to FP32 with sc = emin32d - F.
 template <int CH, bool LIN2>
 __device__ __forceinline__ void row_q2_f32x(const DevSector& S, const DevTermsQ2& H, const uint64_t* off_s,
-                                            const uint64_t* str_s, const uint64_t* wm, uint64_t i,
+                                            const uint64_t* str_s, const uint64_t* wm, uint64_t i, uint64_t s,
                                             const int* __restrict__ X, int ld, int col0, int ch, const int* sc,
                                             float* __restrict__ y) {
-    const uint64_t s = d_unrank(S, off_s, str_s, i);
     long long md = H.MC32;
     if (H.Mlin32) {
         uint64_t m = s;
