@@ -161,8 +161,28 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
  * fields, at most two distinct hop amplitudes and four distinct Sz Sz coefficients, dyadic
  * coefficients), 0 for the general kernels (any Q, partition and nrhs). Both sum exactly in fixed
  * point (see dq_matvec) and compute the same y up to the rounding of the coefficients to their
- * integer grid, which is exact on the panel path. */
+ * integer grid, which is exact on the panel path. Terms made by dq_make_cluster_terms report 2
+ * (the cluster-merged kernel). */
 int dq_terms_path(const dq_terms* t, int* path);
+
+/* Compile terms in the cluster-merged form of App. C instead: the terms are grouped into clusters
+ * of at most `cluster_sites` sites (clusters may overlap; each term goes to the first cluster that
+ * holds its sites or can take them, in the order of the terms sorted by their sites), and all the
+ * terms of one cluster are merged into one sparse matrix over the cluster's digit patterns
+ * (Nbits * cluster_sites <= 12 bits, i.e. at most 4096 patterns), stored column by column: each
+ * entry holds the XOR mask that moves a word between the two patterns and the merged coefficient
+ * (one integer grid for all, as in dq_matvec). dq_matvec then applies one column per cluster and
+ * row (any Q, one- or two-word states, 1..64 right-hand sides, both dtypes in exact fixed point
+ * with 57-bit x), and dq_terms_path reports 2. Results equal those of dq_make_terms up to the
+ * rounding of the merged coefficients to the grid. Errors: as dq_make_terms; DQ_EINVAL for
+ * cluster_sites out of [2, 12] or Nbits * cluster_sites > 12, or more than 64 clusters.
+ * Synchronous; *out is owned by the caller (dq_free_terms). */
+int dq_make_cluster_terms(const dq_sector* s, const dq_term* terms, int n_terms, int cluster_sites, dq_terms** out);
+
+/* Clusters of terms made by dq_make_cluster_terms: their number, the sites of each (host array
+ * of 12 ints per cluster, -1 after the last site; may be NULL) and the largest number of matrix
+ * entries one row can meet (may be NULL). DQ_EINVAL for terms in another form. */
+int dq_cluster_info(const dq_terms* t, int* n_clusters, int* sites, int* entries);
 
 /* Release compiled terms. NULL is allowed. */
 void dq_free_terms(dq_terms* t);

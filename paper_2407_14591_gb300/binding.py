@@ -29,7 +29,7 @@ EXPORTED = (
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
     "dq_state_at2", "dq_index_of2", "dq_next_state2", "dq_state_at_batch2", "dq_index_of_batch2",
     "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_matvec_noalloc",
-    "dq_lanczos", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free", "dq_term_grads",
+    "dq_lanczos", "dq_make_cluster_terms", "dq_cluster_info", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free", "dq_term_grads",
     "dq_timing_enable", "dq_timing_read",
 )
 
@@ -69,6 +69,8 @@ def _load() -> ctypes.CDLL:
         "dq_check_device": (i32, [vp, vp]),
         "dq_make_terms": (i32, [vp, P(_Term), i32, P(vp)]),
         "dq_free_terms": (None, [vp]),
+        "dq_make_cluster_terms": (i32, [vp, P(_Term), i32, i32, P(vp)]),
+        "dq_cluster_info": (i32, [vp, P(i32), P(i32), P(i32)]),
         "dq_terms_path": (i32, [vp, P(i32)]),
         "dq_matvec": (i32, [vp, vp, vp, vp, i32, i32, vp]),
         "dq_matvec_noalloc": (i32, [vp, vp, vp, vp, i32, vp]),
@@ -236,17 +238,30 @@ def next_state(sector: Sector, state: int) -> int:
 
 
 class Terms:
-    """Operator terms compiled for one sector; ``terms`` is a list of (kind, i, j, coef)."""
+    """Operator terms compiled for one sector; ``terms`` is a list of (kind, i, j, coef). With
+    ``cluster_sites`` the cluster-merged form of App. C (dq_make_cluster_terms)."""
 
-    def __init__(self, sector: Sector, terms):
+    def __init__(self, sector: Sector, terms, cluster_sites: int | None = None):
         arr = (_Term * max(1, len(terms)))()
         for q, (kind, i, j, c) in enumerate(terms):
             k = KINDS[kind] if isinstance(kind, str) else int(kind)
             arr[q] = _Term(k, int(i), int(j), float(c))
         h = ctypes.c_void_p()
-        _check(_lib.dq_make_terms(sector.handle, arr, len(terms), ctypes.byref(h)))
+        if cluster_sites is None:
+            _check(_lib.dq_make_terms(sector.handle, arr, len(terms), ctypes.byref(h)))
+        else:
+            _check(_lib.dq_make_cluster_terms(sector.handle, arr, len(terms), int(cluster_sites), ctypes.byref(h)))
         self._h = h
         self.sector = sector  # keeps the sector alive while the terms exist
+
+    def clusters(self):
+        """(list of site lists, largest number of entries a row meets) of cluster-merged terms."""
+        n = ctypes.c_int()
+        _check(_lib.dq_cluster_info(self._h, ctypes.byref(n), None, None))
+        sites = (ctypes.c_int * (12 * max(1, n.value)))()
+        ent = ctypes.c_int()
+        _check(_lib.dq_cluster_info(self._h, ctypes.byref(n), sites, ctypes.byref(ent)))
+        return [[v for v in sites[12 * c:12 * c + 12] if v >= 0] for c in range(n.value)], ent.value
 
     @property
     def handle(self):
@@ -254,10 +269,10 @@ class Terms:
 
     @property
     def path(self) -> str:
-        """'panel' or 'general': the product kernel used for one right-hand side."""
+        """'panel', 'general' or 'cluster': the product kernel used for one right-hand side."""
         v = ctypes.c_int()
         _check(_lib.dq_terms_path(self._h, ctypes.byref(v)))
-        return "panel" if v.value == 1 else "general"
+        return {1: "panel", 2: "cluster"}.get(v.value, "general")
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -268,6 +283,10 @@ class Terms:
 
 def make_terms(sector: Sector, terms) -> Terms:
     return Terms(sector, terms)
+
+
+def make_cluster_terms(sector: Sector, terms, cluster_sites: int) -> Terms:
+    return Terms(sector, terms, cluster_sites)
 
 
 def _dtype_code(t) -> int:

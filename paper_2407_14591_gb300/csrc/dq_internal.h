@@ -153,6 +153,25 @@ struct PanelPlan {
     const uint64_t* list;
 };
 
+// Cluster-merged operator (App. C): every term lies in one cluster of at most kClMaxSites sites,
+// and the terms of a cluster are merged into one sparse matrix S_c over the cluster's digit
+// patterns (pattern p = sum_k digit(site_k) << (Nbits k)), stored by columns: column p lists the
+// entries (XOR mask that turns a word with cluster pattern p into one with pattern p', and the
+// coefficient S_c[p', p] as an integer M with S = M 2^emin). The diagonal entry has mask 0.
+constexpr int kClMaxSites = 12;  // and Nbits * sites <= 12 (at most 4096 patterns per cluster)
+constexpr int kClMax = 64;
+struct DevTermsCL {
+    int ncl;
+    int emin;
+    const int* nsite;        // [ncl]
+    const int* sh;           // [ncl][kClMaxSites]: bit shift of the digit of cluster site k
+    const int* col_base;     // [ncl]: start of cluster c's column offsets in col_off
+    const uint32_t* col_off; // per cluster 2^(Nbits nsite) + 1 offsets into the entry arrays
+    const uint64_t* dlo;     // entry mask, bits 0..63
+    const uint64_t* dhi;     // entry mask, bits 64..127 (two-word states)
+    const long long* M;      // entry coefficient / 2^emin
+};
+
 // Host-side tables kept by a sector.
 struct HostTables {
     std::vector<uint64_t> Dq;  // (L+1) x (nmax_total+1), saturated at UINT64_MAX
@@ -186,6 +205,9 @@ struct dq_terms {
     std::vector<void*> dev_allocs;
     int max_hops;  // upper bound on off-diagonal elements per row
     bool panel_ok = false;     // the panel product applies (see PanelPlan)
+    bool cluster = false;      // cluster-merged form (App. C), dq_make_cluster_terms
+    dq::DevTermsCL clv;
+    std::vector<int> cl_sites; // host copy: the sites of each cluster, -1 after the last
     dq::PanelPlan pp;
     void* scratch = nullptr;   // fixed-point copy of x and the exponent word, grown on demand
     size_t scratch_bytes = 0;
@@ -211,6 +233,11 @@ int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y,
 // the same batches for states stored as two uint64 words (low word first)
 int launch_state_at_batch_w(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
 int launch_index_of_batch_w(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
+
+// validation shared by the term compilers (dq_terms.cpp): DQ_OK or the error status
+int check_terms(const dq_sector* s, const dq_term* terms, int n_terms);
+// cluster-merged product (dq_cluster.cu)
+int launch_cluster_matvec(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, int nrhs, void* stream);
 
 // panel product (dq_panel.cpp / dq_panel.cu)
 int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,

@@ -1,29 +1,27 @@
 // Lanczos driver for the ground-state energy (Sec. 4.4; App. D calls a native Lanczos): the
 // only use of H is the matrix-free product. Vectors live on the device in the caller's dtype;
-// every dot product, norm and vector update is computed in FP64 with a fixed reduction order (the
-// result does not depend on timing). The tridiagonal matrix T is solved on the host by bisection
-// on its Sturm sequence, and the Ritz vector's coefficients by inverse iteration (own
+// every dot product and norm accumulates in FP64 with a fixed reduction order (the result does
+// not depend on timing). The tridiagonal matrix T is solved on the host by bisection on its
+// Sturm sequence, and the Ritz vector's coefficients by inverse iteration (own
 // implementations).
 //
-// One step, all on the device:
-//   w = H v_k                                     (the product)
-//   alpha_k = <v_k, w>                            (k_gs_dots over one vector)
-//   w -= alpha_k v_k + beta_{k-1} v_{k-1}         (k_three_term, with rho0 = ||w||)
-//   with re-orthogonalisation, classical Gram-Schmidt against v_0 .. v_k:
-//     h = V^T w; w -= V h                         (k_gs_dots, k_gs_update, with rho1 = ||w||)
-//     a second pass only if rho1 < rho0 / sqrt(2) (the DGKS criterion; always with reorth = 2):
-//     the kernels of that pass read the decision from device memory and return at once when
-//     it is not needed
-//   beta_k = ||w||; v_{k+1} = w / beta_k           (k_normalise)
-// The reductions finish in the last block of each kernel (fixed order), the coefficients stay in
-// device memory, and each step copies alpha_k and beta_k^2 into pinned host memory. The host
-// reads step k's values only after it has queued step k+2 (two events in flight), so the GPU
-// never waits for the host; a breakdown found late only costs the steps already queued, whose
-// results are dropped.
-// Work per step: the product, one pass over v_k and v_{k-1}, and with re-orthogonalisation two
-// passes over V = [v_0 .. v_k] (dots, update), four when the second pass runs. The FP64 multiply-
-// adds of those passes (2 D (k+1)) are what bounds a step on this GPU, where FP64 runs at a small
-// fraction of the integer and FP32 rate.
+// One step is two launches: the product w = H v_k, then one cooperative kernel (k_lz_step, all
+// blocks resident, grid-wide barriers between its phases) that does the rest on the device:
+//   alpha_k = <v_k, w>;  w -= alpha_k v_k + beta_{k-1} v_{k-1}      (rho0 = ||w||)
+//   with re-orthogonalisation, classical Gram-Schmidt against V = [v_0 .. v_k]:
+//     h = V^T w; w -= V h                                           (rho1 = ||w||)
+//     a second pass only if rho1 < rho0 / sqrt(2) (the DGKS criterion; always with reorth = 2)
+//   beta_k = ||w||; v_{k+1} = w / beta_k
+// Every block reduces the partial sums itself in the same fixed order, so all blocks hold the
+// same coefficients without another barrier. alpha_k and beta_k^2 go to device arrays and to
+// mapped pinned host memory. The host reads step k's values only after it has queued step k+2,
+// so the GPU never waits for the host; a breakdown found late only costs the steps already
+// queued, whose results are dropped.
+// Arithmetic: FP64 for dot products, norms, the three-term step and (FP64 vectors) the
+// Gram-Schmidt updates; FP32 vectors are widened to FP64 with integer bit operations (exact)
+// and take their Gram-Schmidt updates, whose coefficients are at the level of the vectors' own
+// rounding, as FP32 multiply-adds. The FP64 multiply-adds of the passes over V (2 D (k+1) per
+// step) bound a step on this GPU, whose FP64 rate is a small fraction of its integer rate.
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -76,13 +74,6 @@ __device__ __forceinline__ bool last_block(unsigned* counter) {
     __syncthreads();
     if (last) __threadfence();
     return last;
-}
-
-// Sum of partial[0 .. nb) in a fixed order (strided per thread, then the block tree).
-__device__ __forceinline__ double sum_partials(const double* partial, int nb, double* sh) {
-    double acc = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += __ldcg(partial + b);
-    return block_sum(acc, sh);
 }
 
 // out[j] = <V_j, w> for j < k, V_j = V + j * ldv. Each pass takes kDotTile vectors at once (w is
@@ -140,76 +131,221 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_dots(const T* __restrict__ V
         }
 }
 
-// w[i] -= sum_{j<k} h[j] V_j[i] (FP64 arithmetic, stored in T) and the new ||w||^2 into
-// scal[norm_slot]; the first pass (pass2 == false) also decides whether the second one runs
-// (scal[kPass2]: always with `always2`, else when the norm fell below 1/sqrt(2) of rho0), the
-// second (pass2 == true) does nothing unless scal[kPass2] is set. Both leave the step's final
-// ||w||^2 in scal[kBeta2].
-template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_gs_update(T* __restrict__ w, const T* __restrict__ V, size_t ldv,
-                                                            int k, const double* __restrict__ h, uint64_t n,
-                                                            double* __restrict__ partial, double* scal,
-                                                            unsigned* counter, bool pass2, bool always2) {
-    if (pass2 && scal[kPass2] == 0.0) return;
-    extern __shared__ double hs[];
-    __shared__ double red[32];
-    for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
+// Exact widening of a float to double with integer operations (the hardware conversion runs on
+// the FP64 pipe); zero, subnormals, Inf and NaN take the hardware path.
+__device__ __forceinline__ double widen(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(e + 896u) << 52) |
+                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double widen(double d) { return d; }
+
+constexpr unsigned kBarrierLimit = 1u << 24;  // polls of a grid barrier before it gives up
+
+// Grid-wide barrier of a cooperative launch (every block resident): a counter of arrivals and a
+// generation word. A block waits at most kBarrierLimit polls; on timeout it raises *fail, and
+// every later barrier returns false at once, so the kernel ends with the error recorded.
+__device__ __forceinline__ bool grid_sync(unsigned* bar, int* fail) {
+    __shared__ int ok;
     __syncthreads();
-    double nacc = 0.0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        double acc = (double)w[i];
-        int j = 0;
-        for (; j + 8 <= k; j += 8) {
-            double v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = (double)__ldg(V + (size_t)(j + q) * ldv + i);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc -= hs[j + q] * v[q];
-        }
-        for (; j < k; ++j) acc -= hs[j] * (double)__ldg(V + (size_t)j * ldv + i);
-        const T r = (T)acc;
-        w[i] = r;
-        nacc += (double)r * (double)r;
-    }
-    nacc = block_sum(nacc, red);
-    if (threadIdx.x == 0) partial[blockIdx.x] = nacc;
-    if (last_block(counter)) {
-        const double r2 = sum_partials(partial, gridDim.x, red);
-        if (threadIdx.x == 0) {
-            if (!pass2) {
-                scal[kRho1] = r2;
-                scal[kPass2] = (always2 || r2 < 0.5 * scal[kRho0]) ? 1.0 : 0.0;
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        volatile int* vf = fail;
+        ok = !*vf;
+        if (ok) {
+            const unsigned g = *gen;
+            __threadfence();
+            if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+                bar[0] = 0u;
+                __threadfence();
+                atomicAdd(bar + 1, 1u);
+            } else {
+                unsigned it = 0;
+                while (*gen == g && !*vf && it < kBarrierLimit) {
+                    __nanosleep(64);
+                    ++it;
+                }
+                if (*gen == g) {
+                    *vf = 1;
+                    ok = 0;
+                }
             }
-            scal[kBeta2] = r2;
+            __threadfence();
         }
     }
+    __syncthreads();
+    return ok != 0;
 }
 
-// w -= alpha v + beta u (u may be NULL; alpha = scal[kAlpha], beta^2 = beta2_prev), the new
-// ||w||^2 into scal[kRho0] and scal[kBeta2].
+// Sum of part[0 .. nb) in a fixed order; every block gets the same value.
+__device__ __forceinline__ double reduce_all(const double* part, int nb, double* sh) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += __ldcg(part + b);
+    return block_sum(acc, sh);
+}
+
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_three_term(T* __restrict__ w, const T* __restrict__ v,
-                                                             const T* __restrict__ u, double* scal,
-                                                             const double* __restrict__ beta2_prev, uint64_t n,
-                                                             double* __restrict__ partial, unsigned* counter) {
-    __shared__ double red[32];
-    const double al = scal[kAlpha], be = u ? sqrt(*beta2_prev) : 0.0;
+struct LzStep {
+    const T* V;       // v_0 .. v_k, stride ldv
+    size_t ldv;
+    int k;            // step index
+    T* w;             // H v_k on entry; the new residual on exit
+    T* vnext;         // v_{k+1} (NULL at the last step)
+    uint64_t n;
+    int reorth;       // 0, 1 (DGKS second pass), 2 (second pass always)
+    double* part;     // per-block partial sums, gridDim.x * (2 (k+1) + 8) doubles
+    double* h;        // projection coefficients, k+1 doubles
+    double* alpha;    // alpha_j, beta_j^2 of every step (device)
+    double* beta2;
+    volatile double* host;  // mapped pinned host memory: alpha_k, beta_k^2 at [2k], [2k+1]
+    unsigned* bar;    // grid barrier (two words)
+    int* fail;        // barrier timeout
+};
+
+// h = V^T w over j <= k (partials per block and vector, then block b reduces the vectors
+// j = b, b + nb, ... in block order), followed by w -= V h and the block partials of ||w||^2.
+template <typename T>
+__device__ __forceinline__ bool lz_gram_schmidt(const LzStep<T>& a, double* pd, double* pn, double* hs,
+                                                double* red) {
+    __shared__ double sh[kDotTile][kRedThreads / 32];
+    const int kk = a.k + 1, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    for (int j0 = 0; j0 < kk; j0 += kDotTile) {
+        const int nj = kk - j0 < kDotTile ? kk - j0 : kDotTile;
+        double acc[kDotTile];
+#pragma unroll
+        for (int q = 0; q < kDotTile; ++q) acc[q] = 0.0;
+        const T* Vb = a.V + (size_t)j0 * a.ldv;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step) {
+            const double wi = widen(a.w[i]);
+#pragma unroll
+            for (int q = 0; q < kDotTile; ++q)
+                if (q < nj) acc[q] += widen(__ldg(Vb + (size_t)q * a.ldv + i)) * wi;
+        }
+#pragma unroll
+        for (int q = 0; q < kDotTile; ++q) {
+            double v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[q][wid] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < nj) {
+            double sum = 0.0;
+            for (int r = 0; r < kRedThreads / 32; ++r) sum += sh[threadIdx.x][r];
+            pd[(size_t)blockIdx.x * kk + j0 + threadIdx.x] = sum;
+        }
+        __syncthreads();
+    }
+    if (!grid_sync(a.bar, a.fail)) return false;
+    for (int j = blockIdx.x; j < kk; j += gridDim.x) {
+        double acc = 0.0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += __ldcg(pd + (size_t)b * kk + j);
+        acc = block_sum(acc, red);
+        if (threadIdx.x == 0) a.h[j] = acc;
+    }
+    if (!grid_sync(a.bar, a.fail)) return false;
+    for (int q = threadIdx.x; q < kk; q += blockDim.x) hs[q] = __ldcg(a.h + q);
+    __syncthreads();
     double nacc = 0.0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        double acc = (double)w[i] - al * (double)v[i];
-        if (u) acc -= be * (double)u[i];
-        const T r = (T)acc;
-        w[i] = r;
-        nacc += (double)r * (double)r;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step) {
+        T r;
+        if constexpr (sizeof(T) == 8) {
+            double acc = a.w[i];
+            int j = 0;
+            for (; j + 8 <= kk; j += 8) {
+                double v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = __ldg(a.V + (size_t)(j + q) * a.ldv + i);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc -= hs[j + q] * v[q];
+            }
+            for (; j < kk; ++j) acc -= hs[j] * __ldg(a.V + (size_t)j * a.ldv + i);
+            r = acc;
+        } else {
+            float corr = 0.f;
+            int j = 0;
+            for (; j + 8 <= kk; j += 8) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) v[q] = __ldg(a.V + (size_t)(j + q) * a.ldv + i);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) corr = fmaf((float)hs[j + q], v[q], corr);
+            }
+            for (; j < kk; ++j) corr = fmaf((float)hs[j], __ldg(a.V + (size_t)j * a.ldv + i), corr);
+            r = a.w[i] - corr;
+        }
+        a.w[i] = r;
+        const double rd = widen(r);
+        nacc += rd * rd;
     }
     nacc = block_sum(nacc, red);
-    if (threadIdx.x == 0) partial[blockIdx.x] = nacc;
-    if (last_block(counter)) {
-        const double r2 = sum_partials(partial, gridDim.x, red);
-        if (threadIdx.x == 0) {
-            scal[kRho0] = r2;
-            scal[kBeta2] = r2;
+    if (threadIdx.x == 0) pn[blockIdx.x] = nacc;
+    return grid_sync(a.bar, a.fail);
+}
+
+// One Lanczos step after the product (see the file comment). Cooperative launch; dynamic shared
+// memory: k + 1 doubles (the projection coefficients).
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_lz_step(LzStep<T> a) {
+    extern __shared__ double hs[];
+    __shared__ double red[32];
+    const int nb = gridDim.x;
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    double* p_alpha = a.part;
+    double* p_rho0 = a.part + nb;
+    double* p_rho1 = a.part + 2 * nb;
+    double* p_rho2 = a.part + 3 * nb;
+    double* p_dots = a.part + 4 * nb;  // nb * kk
+    const T* vk = a.V + (size_t)a.k * a.ldv;
+    const T* vp = a.k ? a.V + (size_t)(a.k - 1) * a.ldv : nullptr;
+    // alpha_k = <v_k, w>
+    double acc = 0.0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step)
+        acc += widen(__ldg(vk + i)) * widen(a.w[i]);
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) p_alpha[blockIdx.x] = acc;
+    if (!grid_sync(a.bar, a.fail)) return;
+    const double al = reduce_all(p_alpha, nb, red);
+    const double be = vp ? sqrt(__ldcg(a.beta2 + a.k - 1)) : 0.0;
+    // three-term step, rho0^2
+    acc = 0.0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step) {
+        double r = widen(a.w[i]) - al * widen(__ldg(vk + i));
+        if (vp) r -= be * widen(__ldg(vp + i));
+        const T rt = (T)r;
+        a.w[i] = rt;
+        const double rd = widen(rt);
+        acc += rd * rd;
+    }
+    acc = block_sum(acc, red);
+    if (threadIdx.x == 0) p_rho0[blockIdx.x] = acc;
+    if (!grid_sync(a.bar, a.fail)) return;
+    double b2 = reduce_all(p_rho0, nb, red);
+    if (a.reorth) {
+        const double rho0 = b2;
+        if (!lz_gram_schmidt(a, p_dots, p_rho1, hs, red)) return;
+        b2 = reduce_all(p_rho1, nb, red);
+        if (a.reorth == 2 || b2 < 0.5 * rho0) {
+            if (!lz_gram_schmidt(a, p_dots, p_rho2, hs, red)) return;
+            b2 = reduce_all(p_rho2, nb, red);
         }
+    }
+    // beta_k, v_{k+1}
+    if (a.vnext) {
+        const double sc = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step)
+            a.vnext[i] = (T)(sc * widen(a.w[i]));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        a.alpha[a.k] = al;
+        a.beta2[a.k] = b2;
+        a.host[2 * a.k] = al;
+        a.host[2 * a.k + 1] = b2;
+        __threadfence_system();
     }
 }
 
@@ -366,35 +502,54 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     const uint64_t D = s->D;
     const size_t ldv = (D + 31) & ~(size_t)31;
     const int sms = sm_count_cached();
-    const int nbd = 2 * sms;  // blocks of the dot kernel (one partial per vector each)
-    const int nbu = 8 * sms;  // blocks of the streaming kernels
+    int dev = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop) return set_error(DQ_ECUDA, "Lanczos: the device does not support cooperative launches");
+    const size_t hsm = (size_t)(steps + 1) * sizeof(double);
+    auto kern = k_lz_step<T>;
+    if (hsm > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm) != cudaSuccess)
+        return set_error(DQ_ECUDA, "Lanczos: shared memory for %d coefficients", steps + 1);
+    int per_sm = occupancy_cached(reinterpret_cast<const void*>(kern), kRedThreads, hsm);
+    if (per_sm > 4) per_sm = 4;
+    const int nb = per_sm * sms;  // blocks of the cooperative step kernel (all resident)
+    const int nbd = 2 * sms;      // blocks of the start-vector reduction
     int rc = DQ_OK;
     Work ws;
     T* V = (T*)ws.get((size_t)(steps + 1) * ldv * sizeof(T), rc);
     if (!V) return rc;
     T* w = (T*)ws.get(ldv * sizeof(T), rc);
     if (!w) return rc;
-    double* partial = (double*)ws.get((size_t)((steps + 1) * nbd + nbu) * sizeof(double), rc);
-    if (!partial) return rc;
-    // device doubles: h[0 .. steps], then the scalars; counters of the last-block reductions
-    double* dd = (double*)ws.get((size_t)(steps + 1 + kNScal) * sizeof(double), rc);
+    const size_t npart = (size_t)nb * (steps + 6) > (size_t)nbd ? (size_t)nb * (steps + 6) : (size_t)nbd;
+    double* part = (double*)ws.get(npart * sizeof(double), rc);
+    if (!part) return rc;
+    // device doubles: h[0 .. steps], alpha[0 .. steps), beta2[0 .. steps), ||v0||^2
+    double* dd = (double*)ws.get((size_t)(3 * steps + 4) * sizeof(double), rc);
     if (!dd) return rc;
     double* hv = dd;
-    double* scal = dd + (steps + 1);
-    unsigned* counter = (unsigned*)ws.get(4 * sizeof(unsigned), rc);
-    if (!counter) return rc;
-    double* beta2_prev = (double*)ws.get(sizeof(double), rc);  // beta_{k-1}^2 for the three-term step
-    if (!beta2_prev) return rc;
-    double* hst = (double*)ws.get_host((size_t)2 * steps * sizeof(double), rc);  // alpha_k, beta_k^2
-    if (!hst) return rc;
-    const int nev = 3;
-    for (int q = 0; q < nev; ++q) {
+    double* alpha_d = dd + (steps + 1);
+    double* beta2_d = alpha_d + steps;
+    double* v0n = beta2_d + steps;
+    int* ictl = (int*)ws.get(8 * sizeof(int), rc);  // barrier (2 words), fail flag, start-vector counter
+    if (!ictl) return rc;
+    // alpha_k, beta_k^2 of every step, written by the step kernel into mapped pinned memory
+    double* hst = nullptr;
+    {
+        cudaError_t e = cudaHostAlloc((void**)&hst, (size_t)2 * steps * sizeof(double), cudaHostAllocMapped);
+        if (e != cudaSuccess) return set_error(DQ_ENOMEM, "Lanczos cudaHostAlloc: %s", cudaGetErrorString(e));
+        ws.host_allocs.push_back(hst);
+    }
+    double* hst_dev = nullptr;
+    if (cudaHostGetDevicePointer((void**)&hst_dev, hst, 0) != cudaSuccess)
+        return set_error(DQ_ECUDA, "Lanczos: no device address for mapped host memory");
+    for (int q = 0; q < 3; ++q) {
         cudaEvent_t e;
         if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
             return set_error(DQ_ECUDA, "Lanczos: cudaEventCreate failed");
         ws.events.push_back(e);
     }
-    cudaMemsetAsync(counter, 0, 4 * sizeof(unsigned), st);
+    cudaMemsetAsync(ictl, 0, 8 * sizeof(int), st);
     const int dtype = sizeof(T) == 8 ? DQ_F64 : DQ_F32;
     auto cuda_fail = [&](const char* what) -> int {
         cudaError_t e = cudaGetLastError();
@@ -402,62 +557,63 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
         return DQ_OK;
     };
 
-    // v_0 = v0 / ||v0||
-    k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(v0, ldv, 1, v0, D, partial, scal + kV0, counter, nullptr);
+    // v_0 = v0 / ||v0|| (last-block reduction; its counter is ictl[4])
+    k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(v0, ldv, 1, v0, D, part, v0n, (unsigned*)(ictl + 4), nullptr);
     double nrm2 = 0.0;
-    cudaError_t e = cudaMemcpyAsync(&nrm2, scal + kV0, sizeof(double), cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaMemcpyAsync(&nrm2, v0n, sizeof(double), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos start vector: %s", cudaGetErrorString(e));
     if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) return set_error(DQ_EINVAL, "v0 has zero or non-finite norm");
-    k_normalise<T><<<nbu, kRedThreads, 0, st>>>(V, v0, scal + kV0, D);
-    cudaMemsetAsync(beta2_prev, 0, sizeof(double), st);
+    k_normalise<T><<<8 * sms, kRedThreads, 0, st>>>(V, v0, v0n, D);
+
+    LzStep<T> arg;
+    arg.ldv = ldv;
+    arg.V = V;
+    arg.w = w;
+    arg.n = D;
+    arg.reorth = reorth;
+    arg.part = part;
+    arg.h = hv;
+    arg.alpha = alpha_d;
+    arg.beta2 = beta2_d;
+    arg.host = hst_dev;
+    arg.bar = (unsigned*)ictl;
+    arg.fail = ictl + 2;
 
     std::vector<double> a, b;
     double tnorm = 0.0, bprev = 0.0;
     int m = 0;
     bool stop = false;
-    // host side of step q: read its coefficients (its event has completed) and test for breakdown
+    // host side of step q: its event has completed, so its coefficients are in hst
     auto consume = [&](int q) -> int {
-        cudaError_t ee = cudaEventSynchronize(ws.events[q % nev]);
+        cudaError_t ee = cudaEventSynchronize(ws.events[q % 3]);
         if (ee != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos step: %s", cudaGetErrorString(ee));
         if (stop) return DQ_OK;
-        const double al = hst[2 * q], be = std::sqrt(hst[2 * q + 1]);
+        const double al = ((volatile double*)hst)[2 * q], be = std::sqrt(((volatile double*)hst)[2 * q + 1]);
+        if (!std::isfinite(al) || !std::isfinite(be)) return set_error(DQ_ECUDA, "Lanczos: non-finite coefficient");
         a.push_back(al);
         b.push_back(be);
         m = q + 1;
         tnorm = std::fmax(tnorm, std::fmax(std::fabs(al), std::fmax(be, bprev)));
         bprev = be;
-        if (!std::isfinite(al) || !std::isfinite(be)) return set_error(DQ_ECUDA, "Lanczos: non-finite coefficient");
         if (be < 1e-14 * tnorm) stop = true;
         return DQ_OK;
     };
     int queued = 0;
     for (int k = 0; k < steps; ++k) {
-        if (k >= 2) {  // step k-2 done: the GPU still has step k-1 queued
+        if (k >= 2) {  // step k-2 is done; the GPU still has step k-1 queued
             if ((rc = consume(k - 2))) return rc;
             if (stop) break;
         }
         T* vk = V + (size_t)k * ldv;
         int le = launch_matvec(s, t, vk, w, dtype, 1, st);
         if (le) return set_error(DQ_ECUDA, "matvec launch: %s", cudaGetErrorString((cudaError_t)le));
-        k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(vk, ldv, 1, w, D, partial, scal + kAlpha, counter, nullptr);
-        k_three_term<T><<<nbu, kRedThreads, 0, st>>>(w, vk, k ? V + (size_t)(k - 1) * ldv : nullptr, scal,
-                                                    beta2_prev, D, partial, counter + 1);
-        if (reorth) {
-            const int kk = k + 1;
-            const size_t hsm = (size_t)kk * sizeof(double);
-            for (int pass = 0; pass < 2; ++pass) {
-                k_gs_dots<T><<<nbd, kRedThreads, 0, st>>>(V, ldv, kk, w, D, partial, hv, counter + 2,
-                                                         pass ? scal + kPass2 : nullptr);
-                k_gs_update<T><<<nbu, kRedThreads, hsm, st>>>(w, V, ldv, kk, hv, D, partial + (size_t)kk * nbd, scal,
-                                                             counter + 3, pass == 1, reorth == 2);
-            }
-        }
-        if (k + 1 < steps) k_normalise<T><<<nbu, kRedThreads, 0, st>>>(V + (size_t)(k + 1) * ldv, w, scal + kBeta2, D);
-        cudaMemcpyAsync(beta2_prev, scal + kBeta2, sizeof(double), cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(hst + 2 * k, scal + kAlpha, sizeof(double), cudaMemcpyDeviceToHost, st);
-        cudaMemcpyAsync(hst + 2 * k + 1, scal + kBeta2, sizeof(double), cudaMemcpyDeviceToHost, st);
-        cudaEventRecord(ws.events[k % nev], st);
+        arg.k = k;
+        arg.vnext = k + 1 < steps ? V + (size_t)(k + 1) * ldv : nullptr;
+        void* args[] = {&arg};
+        e = cudaLaunchCooperativeKernel((const void*)kern, dim3(nb), dim3(kRedThreads), args, (size_t)(k + 1) * 8, st);
+        if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos step launch: %s", cudaGetErrorString(e));
+        cudaEventRecord(ws.events[k % 3], st);
         if ((rc = cuda_fail("step"))) return rc;
         queued = k + 1;
     }
@@ -465,6 +621,11 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
         if (q < m) continue;
         if ((rc = consume(q))) return rc;
     }
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos: %s", cudaGetErrorString(e));
+    int ctl[4] = {0, 0, 0, 0};
+    cudaMemcpy(ctl, ictl, sizeof ctl, cudaMemcpyDeviceToHost);
+    if (ctl[2]) return set_error(DQ_ECUDA, "Lanczos: a grid barrier of the step kernel timed out");
     if (m == 0) return set_error(DQ_ECUDA, "Lanczos: no step completed");
     std::vector<double> off(b.begin(), b.begin() + (m - 1));
     const double e0 = m == 1 ? a[0] : tridiag_min_eig(a, off);
@@ -473,11 +634,11 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
         std::vector<double> y = m == 1 ? std::vector<double>{1.0} : tridiag_eigvec(a, off, e0);
         e = cudaMemcpyAsync(hv, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos Ritz vector: %s", cudaGetErrorString(e));
-        k_combination<T><<<nbu, kRedThreads, (size_t)m * sizeof(double), st>>>(psi, V, ldv, m, hv, D);
+        k_combination<T><<<8 * sms, kRedThreads, (size_t)m * sizeof(double), st>>>(psi, V, ldv, m, hv, D);
         if ((rc = cuda_fail("Ritz vector"))) return rc;
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos: %s", cudaGetErrorString(e));
     }
-    e = cudaStreamSynchronize(st);
-    if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos: %s", cudaGetErrorString(e));
     if (alpha_out)
         for (int k = 0; k < m; ++k) alpha_out[k] = a[k];
     if (beta_out)

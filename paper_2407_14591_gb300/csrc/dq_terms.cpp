@@ -416,16 +416,7 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
     return DQ_OK;
 }
 
-}  // namespace dq
-
-using namespace dq;
-
-extern "C" {
-
-int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_terms** out) {
-    clear_error();
-    if (!s || !out || (n_terms > 0 && !terms) || n_terms < 0) return set_error(DQ_EINVAL, "bad argument");
-    *out = nullptr;
+int check_terms(const dq_sector* s, const dq_term* terms, int n_terms) {
     for (int q = 0; q < n_terms; ++q) {
         const dq_term& u = terms[q];
         if (u.kind < DQ_XY || u.kind > DQ_U) return set_error(DQ_EINVAL, "term %d: unknown kind %d", q, u.kind);
@@ -437,6 +428,20 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
         if (spin && s->Q != 2) return set_error(DQ_EINVAL, "term %d: spin-1/2 kinds need Q = 2", q);
         if (!std::isfinite(u.coef)) return set_error(DQ_EINVAL, "term %d: coefficient is not finite", q);
     }
+    return DQ_OK;
+}
+
+}  // namespace dq
+
+using namespace dq;
+
+extern "C" {
+
+int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_terms** out) {
+    clear_error();
+    if (!s || !out || (n_terms > 0 && !terms) || n_terms < 0) return set_error(DQ_EINVAL, "bad argument");
+    *out = nullptr;
+    if (int rc = check_terms(s, terms, n_terms)) return rc;
     dq_terms* t = new (std::nothrow) dq_terms();
     if (!t) return set_error(DQ_ENOMEM, "host allocation");
     t->sector = s;
@@ -461,7 +466,7 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
 int dq_terms_path(const dq_terms* t, int* path) {
     clear_error();
     if (!t || !path) return set_error(DQ_EINVAL, "NULL argument");
-    *path = t->panel_ok ? 1 : 0;
+    *path = t->cluster ? 2 : (t->panel_ok ? 1 : 0);
     return DQ_OK;
 }
 

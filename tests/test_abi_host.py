@@ -156,3 +156,29 @@ def test_two_word_forms():
         assert lib.dq_state_at2(n.handle, ctypes.c_uint64(i), st2) == b.DQ_OK
         assert st2[1] == 0 and st2[0] == n.state_at(i)
         assert lib.dq_index_of2(n.handle, st2, ctypes.byref(out)) == b.DQ_OK and out.value == i
+
+
+def test_cluster_terms_host_side():
+    """App. C clusters: every term lies inside one cluster of at most m sites, the clusters cover
+    the lattice, and invalid cluster sizes are refused."""
+    L = 30
+    terms = wl.heisenberg_terms(wl.chain_bonds(L), 1.0) + wl.field_terms(np.linspace(-1, 1, L))
+    s = b.make_sector(L, 2, 15, 2)
+    t = b.make_cluster_terms(s, terms, 11)
+    assert t.path == "cluster"
+    clusters, entries = t.clusters()
+    assert all(len(c) <= 11 for c in clusters) and 3 <= len(clusters) <= 4
+    assert sorted(set(x for c in clusters for x in c)) == list(range(L))
+    for kind, i, j, _ in terms:
+        sites = {i} if j < 0 else {i, j}
+        assert any(sites <= set(c) for c in clusters)
+    assert entries >= len(clusters)  # at least the diagonal of every cluster
+    for m in (1, 13):
+        with pytest.raises(b.DQError) as e:
+            b.make_cluster_terms(s, terms, m)
+        assert e.value.code == b.DQ_EINVAL
+    s4 = b.make_sector(8, 4, 8, 2)
+    with pytest.raises(b.DQError):
+        b.make_cluster_terms(s4, [("HOP", 0, 1, 1.0)], 7)  # 7 sites of 2 bits > 12 bits
+    t4 = b.make_cluster_terms(s4, [("HOP", i, (i + 1) % 8, 1.0) for i in range(8)], 6)
+    assert all(len(c) <= 6 for c in t4.clusters()[0])
