@@ -113,6 +113,14 @@ constexpr int kPanelMaxGroups = 16;
 constexpr int kPanelMaxA = 2;  // distinct hop amplitudes
 constexpr int kPanelMaxK = 4;  // distinct [s_i != s_j] coefficients
 constexpr int kPanelMaxList = kPanelMaxBonds + kPanelMaxGroups;
+// Per-panel values shared by all rows of the panel: counts of [s_i != s_j] over the Sz Sz bonds
+// inside P_0 per coefficient class, and the bit-plane counters (3 bits per position b of P_1) of
+// the Sz Sz bonds across the cut, for s_a = 0 (w0: counts b occupied) and s_a = 1 (w1: b empty).
+struct PanelDiag {
+    int cnt0[kPanelMaxK];
+    uint32_t w0[kPanelMaxK][3], w1[kPanelMaxK][3];
+};
+
 struct PanelPlan {
     int L0, L1, N;
     uint32_t npanels;
@@ -151,6 +159,7 @@ struct PanelPlan {
     const uint32_t* list_off;
     const uint32_t* list_hdr;   // bits 0-7: class-0 P_0 partners, 8-15: class-1, 16-23: crossing
     const uint64_t* list;
+    const PanelDiag* diag;      // per panel, built on the host
 };
 
 // Cluster-merged operator (App. C): every term lies in one cluster of at most kClMaxSites sites,

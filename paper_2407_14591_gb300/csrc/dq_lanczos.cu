@@ -46,6 +46,7 @@ enum : int {
     kNScal = 8,
 };
 
+// Sum of v over the block; the total is returned in thread 0 only (sh: 32 doubles).
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -181,11 +182,17 @@ __device__ __forceinline__ bool grid_sync(unsigned* bar, int* fail) {
     return ok != 0;
 }
 
-// Sum of part[0 .. nb) in a fixed order; every block gets the same value.
+// Sum of part[0 .. nb) in a fixed order, returned to every thread of the block (sh: at least 33
+// doubles); every block gets the same value.
 __device__ __forceinline__ double reduce_all(const double* part, int nb, double* sh) {
     double acc = 0.0;
     for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += __ldcg(part + b);
-    return block_sum(acc, sh);
+    acc = block_sum(acc, sh);  // the total is in thread 0
+    if (threadIdx.x == 0) sh[32] = acc;
+    __syncthreads();
+    acc = sh[32];
+    __syncthreads();
+    return acc;
 }
 
 template <typename T>
@@ -292,7 +299,7 @@ __device__ __forceinline__ bool lz_gram_schmidt(const LzStep<T>& a, double* pd, 
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_lz_step(LzStep<T> a) {
     extern __shared__ double hs[];
-    __shared__ double red[32];
+    __shared__ double red[33];
     const int nb = gridDim.x;
     const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
     double* p_alpha = a.part;

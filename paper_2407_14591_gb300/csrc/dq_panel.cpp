@@ -211,6 +211,30 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
     }
     P.npanels = (uint32_t)ps0.size();
     P.cmax = cmax;
+    // per-panel diagonal counters (see PanelDiag)
+    std::vector<PanelDiag> pdiag(ps0.size());
+    for (size_t q = 0; q < ps0.size(); ++q) {
+        const uint32_t s0 = ps0[q];
+        PanelDiag& g = pdiag[q];
+        std::memset(&g, 0, sizeof g);
+        for (int k = 0; k < P.nK; ++k) {
+            for (int l = (k ? P.p0z_end[k - 1] : 0); l < P.p0z_end[k]; ++l)
+                g.cnt0[k] += __builtin_popcount(s0 & P.p0z_mask[l]) == 1;
+            int c0[32] = {0}, c1[32] = {0};  // per position b of P_1: bonds with s_a = 0 / s_a = 1
+            for (int l = (k ? P.xz_end[k - 1] : 0); l < P.xz_end[k]; ++l) {
+                const int b = __builtin_ctz(P.xz_bbit[l]);
+                if (s0 & P.xz_abit[l])
+                    ++c1[b];
+                else
+                    ++c0[b];
+            }
+            for (int b = 0; b < 32; ++b)
+                for (int qq = 0; qq < 3; ++qq) {
+                    g.w0[k][qq] |= (uint32_t)((c0[b] >> qq) & 1) << b;
+                    g.w1[k][qq] |= (uint32_t)((c1[b] >> qq) & 1) << b;
+                }
+        }
+    }
     // per-panel source lists
     std::vector<uint32_t> loff(ps0.size() + 1, 0), lhdr(ps0.size(), 0);
     std::vector<uint64_t> lst;
@@ -253,6 +277,8 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
     P.list_hdr = (const uint32_t*)p;
     if ((rc = dev_upload(t->dev_allocs, lst.data(), lst.size() * 8, &p))) return rc;
     P.list = (const uint64_t*)p;
+    if ((rc = dev_upload(t->dev_allocs, pdiag.data(), pdiag.size() * sizeof(PanelDiag), &p))) return rc;
+    P.diag = (const PanelDiag*)p;
     P.c0 = s->dev.c0_tab;
     t->panel_ok = true;
     return DQ_OK;

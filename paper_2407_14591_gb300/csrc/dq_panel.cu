@@ -194,13 +194,6 @@ __device__ __forceinline__ uint32_t lds_u16(const unsigned char* sm, uint32_t of
     return (uint32_t)*reinterpret_cast<const uint16_t*>(sm + off);
 }
 
-// Per-panel values shared by all rows: diagonal counts from P_0 and the bit-plane counters of
-// the Sz Sz bonds across the cut.
-struct PanelDiag {
-    int cnt0[kPanelMaxK];
-    uint32_t w0[kPanelMaxK][3], w1[kPanelMaxK][3];
-};
-
 struct PanelCtx {
     uint32_t s0;
     uint64_t start;
@@ -413,7 +406,7 @@ __global__ void __launch_bounds__(kPT, 1)
         pc.start = P.panel_start[pi];
         pc.n1 = P.N - __popc(pc.s0);
         pc.C = (int)P.t1len[pc.n1];
-        // warp 0: source list into shared memory and the first copies; warps 1..: diagonal counters
+        // warp 0: source list into shared memory and the first copies; warp 1: diagonal counters
         if (tid < 32) {
             const uint32_t lo = __ldg(P.list_off + pi), hi = __ldg(P.list_off + pi + 1);
             for (uint32_t q = lo + tid; q < hi; q += 32) lst[q - lo] = __ldg(P.list + q);
@@ -427,35 +420,9 @@ __global__ void __launch_bounds__(kPT, 1)
                 for (int j = 0; j < pq.nx && j < R - 1; ++j)
                     issue_cut<XT, R>(j, 1 + j, P, pq, X, smem, bstride, bar, lst, rg);
             }
-        } else if (tid < 32 + kPanelMaxK) {
-            const int k = tid - 32;
-            int c0 = 0;
-            uint32_t w0[3] = {0u, 0u, 0u}, w1[3] = {0u, 0u, 0u};
-            if (k < P.nK) {
-                for (int l = (k ? P.p0z_end[k - 1] : 0); l < P.p0z_end[k]; ++l) c0 += (__popc(pc.s0 & P.p0z_mask[l]) == 1);
-                for (int l = (k ? P.xz_end[k - 1] : 0); l < P.xz_end[k]; ++l) {
-                    // [s_a != s_b]: with s_a = 0 it counts b occupied (w0), with s_a = 1 b empty (w1);
-                    // each is a 3-bit counter per position b, kept as bit planes
-                    const uint32_t bb = P.xz_bbit[l];
-                    const bool one = (pc.s0 & P.xz_abit[l]) != 0;
-                    uint32_t c = one ? 0u : bb, c1 = one ? bb : 0u;
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        uint32_t t = w0[q] & c;
-                        w0[q] ^= c;
-                        c = t;
-                        uint32_t tb = w1[q] & c1;
-                        w1[q] ^= c1;
-                        c1 = tb;
-                    }
-                }
-            }
-            dg.cnt0[k] = c0;
-#pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                dg.w0[k][q] = w0[q];
-                dg.w1[k][q] = w1[q];
-            }
+        } else if (tid < 32 + (int)(sizeof(PanelDiag) / 4)) {
+            // the panel's diagonal counters, built on the host
+            reinterpret_cast<uint32_t*>(&dg)[tid - 32] = __ldg(reinterpret_cast<const uint32_t*>(P.diag + pi) + tid - 32);
         }
         // the panel's own x: plain coalesced loads into slot 0 (element c at kOwn + c*size)
         {
