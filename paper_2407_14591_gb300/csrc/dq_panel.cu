@@ -17,6 +17,7 @@
 // are not skipped but pointed at a slot that holds zero: no branches, and all such lanes read one
 // address. Every y element is written once, by one thread.
 #include <cstdint>
+#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -257,51 +258,58 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
 #pragma unroll
         for (int k = 0; k < NA; ++k) acc[k][e] = 0;
     }
-    // hops inside P_0: partner panels element by element (two partners per step for more loads
-    // in flight)
-#pragma unroll
-    for (int k = 0; k < NA; ++k) {
-        const int l0 = k ? pc.ncls0 : 0, l1 = k ? pc.np0 : pc.ncls0;
-        int l = l0;
-        for (; l + 1 < l1; l += 2) {
+    // The work of the panel in units that need no copy: P_0 partner panels two at a time (per
+    // amplitude class), and P_1 bond layers. They are interleaved with the cross partners of
+    // the copy ring, so that each bulk copy lands while the warps work on units.
+    const int n0a = (pc.ncls0 + 1) >> 1;                // class-0 P_0 units
+    const int n0u = n0a + ((pc.np0 - pc.ncls0 + 1) >> 1);  // all P_0 units
+    const int nu = n0u + P.n_p1l;
+    auto p0_unit = [&](auto kc, int l, int l1) {
+        constexpr int k = decltype(kc)::value;
+        if (l + 1 < l1) {
             const XT* src = X + lst[l];
             const XT* src2 = X + lst[l + 1];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                int c = tid + e * kPT;
+                const int c = tid + e * kPT;
                 if (c < pc.C) acc[k][e] += (long long)__ldg(src + c) + (long long)__ldg(src2 + c);
             }
-        }
-        if (l < l1) {
+        } else {
             const XT* src = X + lst[l];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                int c = tid + e * kPT;
+                const int c = tid + e * kPT;
                 if (c < pc.C) acc[k][e] += (long long)__ldg(src + c);
             }
         }
-    }
-    // hops inside P_1, layer by layer: a = s ^ (s >> d) marks the active pairs of the layer; rows
+    };
+    // hops inside P_1, one bond layer of distance d: s ^ (s >> d) marks the active pairs; rows
     // whose pair is not active read the zero slot (one address for all of them, so no bank
     // conflicts and no branch)
-    for (int l = 0; l < P.n_p1l; ++l) {
-        const int d = P.p1l_d[l];
-        uint32_t a[E];
+    auto run_unit = [&](int u) {
+        if (u < n0a) {
+            p0_unit(std::integral_constant<int, 0>(), 2 * u, pc.ncls0);
+        } else if (u < n0u) {
+            if constexpr (NA > 1) p0_unit(std::integral_constant<int, NA - 1>(), pc.ncls0 + 2 * (u - n0a), pc.np0);
+        } else {
+            const int l = u - n0u, d = P.p1l_d[l];
 #pragma unroll
-        for (int e = 0; e < E; ++e) a[e] = s2[e] ^ (s2[e] >> d);
+            for (int k = 0; k < NA; ++k) {
+                const int q0 = k ? P.p1l_cut[l] : P.p1l_first[l], q1 = k ? P.p1l_end[l] : P.p1l_cut[l];
+                for (int q = q0; q < q1; ++q) {
+                    const uint32_t lb = P.p1b_lobit[q] << 1, pm2 = P.p1b_pm2[q];
 #pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            const int q0 = k ? P.p1l_cut[l] : P.p1l_first[l], q1 = k ? P.p1l_end[l] : P.p1l_cut[l];
-            for (int q = q0; q < q1; ++q) {
-                const uint32_t lb = P.p1b_lobit[q] << 1, pm2 = P.p1b_pm2[q];
-#pragma unroll
-                for (int e = 0; e < E; ++e) {
-                    const uint32_t t = (a[e] & lb) ? (s2[e] ^ pm2) : kZeroSlot;
-                    acc[k][e] += lds_x<XT>(own, lds_u16(smem, t));
+                    for (int e = 0; e < E; ++e) {
+                        const uint32_t t = ((s2[e] ^ (s2[e] >> d)) & lb) ? (s2[e] ^ pm2) : kZeroSlot;
+                        acc[k][e] += lds_x<XT>(own, lds_u16(smem, t));
+                    }
                 }
             }
         }
-    }
+    };
+    int u = 0;
+    const int lead = pc.nx ? (nu < 2 ? nu : 2) : nu;  // units before the first cross partner
+    for (; u < lead; ++u) run_unit(u);
     // hops across the cut: panel s0 ^ bit_a of the neighbouring block, in the copy ring
     for (int j = 0; j < pc.nx; ++j) {
         const int s = 1 + j % (R - 1);
@@ -327,7 +335,10 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
             }
         }
         release_slot<XT, R>(s, j + R - 1, P, pc, X, smem, bstride, bar, lst, rg);
+        const int target = lead + (int)((long long)(nu - lead) * (j + 1) / pc.nx);
+        for (; u < target; ++u) run_unit(u);
     }
+    for (; u < nu; ++u) run_unit(u);
     // the row result: (C + sum_k K_k n_k) x_i + sum_k A_k S_k, exactly, rounded once
     const uint32_t m1 = (1u << P.L1) - 1u;
 #pragma unroll
