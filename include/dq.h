@@ -270,11 +270,19 @@ int dq_batch_make(int n, const dq_sector* const* sectors, const dq_terms* const*
  * contains no allocation or host synchronisation, so it can be recorded in a CUDA graph. */
 int dq_batch_matvec(dq_batch* b, const void* const* x, void* const* y, void* stream);
 
-/* Autotuner: time every launch shape (threads per CTA, CTAs per SM, rows per tile) on the given
- * vectors (one warm-up and three timed launches each, CUDA events on `stream`), keep the
- * fastest for later dq_batch_matvec calls and return its number in *choice (may be NULL).
- * Overwrites y. Synchronous. */
+/* Autotuner: time every candidate (row mapping, threads per CTA, CTAs per SM, rows per tile) on
+ * the given vectors (one warm-up and three timed launches each, CUDA events on `stream`), keep
+ * the fastest for later dq_batch_matvec calls and return its number in *choice (may be NULL).
+ * The mappings: the CTA's threads take a tile's rows with a block stride and unrank each with
+ * Alg. 4, or each warp takes 32 R consecutive rows and each lane steps from row to row through
+ * the last subsystem's unrank list. Tiles are pulled from an atomic queue in both. Overwrites y.
+ * Synchronous. */
 int dq_batch_tune(dq_batch* b, const void* const* x, void* const* y, void* stream, int* choice);
+
+/* Select candidate `shape` (0 .. *n_shapes - 1) for later dq_batch_matvec calls instead of the
+ * tuned one; a negative shape only reports the number of candidates in *n_shapes (may be NULL).
+ * Errors: DQ_EINVAL. */
+int dq_batch_shape(dq_batch* b, int shape, int* n_shapes);
 
 /* Release a batch plan. NULL is allowed. */
 void dq_batch_free(dq_batch* b);

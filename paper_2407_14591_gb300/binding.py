@@ -29,7 +29,7 @@ EXPORTED = (
     "dq_state_at", "dq_index_of", "dq_next_state", "dq_state_at_batch", "dq_index_of_batch",
     "dq_state_at2", "dq_index_of2", "dq_next_state2", "dq_state_at_batch2", "dq_index_of_batch2",
     "dq_check_device", "dq_make_terms", "dq_terms_path", "dq_free_terms", "dq_matvec", "dq_matvec_noalloc",
-    "dq_lanczos", "dq_make_cluster_terms", "dq_cluster_info", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_free", "dq_term_grads",
+    "dq_lanczos", "dq_make_cluster_terms", "dq_cluster_info", "dq_batch_make", "dq_batch_matvec", "dq_batch_tune", "dq_batch_shape", "dq_batch_free", "dq_term_grads",
     "dq_timing_enable", "dq_timing_read",
 )
 
@@ -78,6 +78,7 @@ def _load() -> ctypes.CDLL:
         "dq_batch_matvec": (i32, [vp, P(vp), P(vp), vp]),
         "dq_batch_tune": (i32, [vp, P(vp), P(vp), vp, P(i32)]),
         "dq_batch_free": (None, [vp]),
+        "dq_batch_shape": (i32, [vp, i32, P(i32)]),
         "dq_term_grads": (i32, [vp, P(_Term), i32, vp, vp, i32, i32, vp, vp]),
         "dq_lanczos": (i32, [vp, vp, vp, i32, i32, i32, P(ctypes.c_double), P(ctypes.c_double),
                              P(ctypes.c_double), P(i32), vp, vp]),
@@ -373,6 +374,16 @@ class Batch:
         xp, yp = self._ptrs(xs, ys)
         _check(_lib.dq_batch_matvec(self._h, xp, yp, _stream_handle()))
         return ys
+
+    def n_shapes(self) -> int:
+        n = ctypes.c_int()
+        _check(_lib.dq_batch_shape(self._h, -1, ctypes.byref(n)))
+        return n.value
+
+    def set_shape(self, shape: int):
+        """Use candidate `shape` (mapping and launch shape) for later products."""
+        _check(_lib.dq_batch_shape(self._h, int(shape), None))
+        self.choice = int(shape)
 
     def tune(self, xs, ys) -> int:
         xp, yp = self._ptrs(xs, ys)

@@ -1,12 +1,18 @@
 // Batched product: y_k = H_k x_k for up to 64 sectors of uneven dimension (different L, N and
 // disorder), each with nrhs right-hand sides, in ONE persistent launch.
 //
-// The rows of all sectors are cut into tiles of `rows_per_tile` rows; tile t belongs to the
-// sector k with prefix[k] <= t < prefix[k+1]. Each CTA walks the tiles with a grid stride, copies
-// the descriptor of the tile's sector into shared memory when the sector changes, and runs the
-// general Q = 2 row computation (Alg. 4 unrank, bond layers, rank by Eq. (index) or Lin's two
-// tables, gather of the nrhs values of x[j], one store of y[i]). The launch shape (threads,
-// CTAs per SM, tile size) is picked by a small autotuner that times each candidate once.
+// The rows of all sectors are cut into tiles; tile t belongs to the sector k with
+// prefix[k] <= t < prefix[k+1]. CTAs pull tiles from an atomic queue (a counter cleared before
+// each launch), copy the descriptor of the tile's sector into shared memory when the sector
+// changes, and run the general Q = 2 row computation (bond layers, rank by Eq. (index) or Lin's
+// two tables, gather of the nrhs values of x[j], one store of y[i]). Two row mappings:
+//   rows    -- the threads of the CTA take the tile's rows with a block stride, each row
+//              unranked with Alg. 4;
+//   walk    -- each warp takes 32 R consecutive rows, lane l the rows l, l + 32, ..., the next
+//              row of a lane from the last subsystem's unrank list (RowWalk: one Alg. 4 per
+//              lane and tile).
+// The autotuner times every (mapping, threads, CTAs per SM, tile) candidate on the caller's
+// vectors and keeps the fastest.
 //
 // Arithmetic: FP64 vectors accumulate in FP64. FP32 vectors use the FP32 copies of the
 // coefficients, form products in FP32 and sum them with Neumaier's compensated summation, so the
@@ -31,8 +37,9 @@ struct BatchItem {
 };
 
 struct BatchParams {
-    int n, nrhs, rows_per_tile;
+    int n, nrhs, rows_per_tile, R;  // R: rows per lane of the walk mapping
     unsigned long long total_tiles;
+    unsigned long long* queue;      // next tile (cleared before the launch)
     unsigned long long prefix[kBatchMax + 1];  // first tile of each sector
     const BatchItem* items;
     const void* x[kBatchMax];
@@ -54,16 +61,102 @@ __device__ __forceinline__ void load_rhs(const T* p, int nr, T* v) {
     for (int c = 0; c < kBatchMaxRhs; ++c) v[c] = c < nr ? __ldg(p + c) : (T)0;
 }
 
+// Row i (word s) of sector (S, H): y[i, :] = sum_j H_ij x[j, :] for the nr right-hand sides.
 template <typename T>
+__device__ __forceinline__ void batch_row(const DevSector& S, const DevTermsQ2& H, const T* __restrict__ x,
+                                          T* __restrict__ y, int nr, uint64_t i, uint64_t s) {
+    const bool lin2 = S.n_sub == 2;
+    const T* posT = sizeof(T) == 8 ? (const T*)H.pos : (const T*)H.posf;
+    // diagonal: FP64 vectors in FP64; FP32 vectors with FP32 coefficients, compensated
+    T dv;
+    if constexpr (sizeof(T) == 8) {
+        double d = H.C;
+        if (H.lin) {
+            uint64_t m = s;
+            while (m) {
+                int p = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                d += __ldg(H.lin + p);
+            }
+        }
+        for (int l = 0; l < H.nl; ++l) {
+            uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+            if (H.kpos[l] < 0) {
+                d += __ldg(H.KA + l) * (double)__popcll(a);
+            } else {
+                while (a) {
+                    int p = __ffsll((long long)a) - 1;
+                    a &= a - 1;
+                    d += __ldg(H.pos + H.kpos[l] + p);
+                }
+            }
+        }
+        dv = d;
+    } else {
+        RowAcc<float> d;
+        d.init(H.Cf);
+        if (H.linf) {
+            uint64_t m = s;
+            while (m) {
+                int p = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                d.add(__ldg(H.linf + p));
+            }
+        }
+        for (int l = 0; l < H.nl; ++l) {
+            uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
+            if (H.kpos[l] < 0) {
+                if (a) d.add(__ldg(H.KAf + l) * (float)__popcll(a));
+            } else {
+                while (a) {
+                    int p = __ffsll((long long)a) - 1;
+                    a &= a - 1;
+                    d.add(__ldg(H.posf + H.kpos[l] + p));
+                }
+            }
+        }
+        dv = d.get();
+    }
+    T xv[kBatchMaxRhs];
+    load_rhs(x + i * nr, nr, xv);
+    RowAcc<T> acc[kBatchMaxRhs];
+#pragma unroll
+    for (int c = 0; c < kBatchMaxRhs; ++c) acc[c].init(c < nr ? dv * xv[c] : (T)0);
+    for (int l = 0; l < H.nl; ++l) {
+        uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
+        const uint64_t pm = 1ull | (1ull << H.dist[l]);
+        const T au = bcf<T>(__ldg(H.KA + kMaxLayers + l), __ldg(H.KAf + kMaxLayers + l));
+        while (o) {
+            int p = __ffsll((long long)o) - 1;
+            o &= o - 1;
+            const uint64_t s2 = s ^ (pm << p);
+            const uint64_t j = lin2 ? d_rank_lin2(S, s2) : d_rank(S, S.off, S.str, s2);
+            const T amp = H.apos[l] < 0 ? au : __ldg(posT + H.apos[l] + p);
+            load_rhs(x + j * nr, nr, xv);
+#pragma unroll
+            for (int c = 0; c < kBatchMaxRhs; ++c)
+                if (c < nr) acc[c].add(amp * xv[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kBatchMaxRhs; ++c)
+        if (c < nr) y[i * nr + c] = acc[c].get();
+}
+
+template <typename T, bool WALK>
 __global__ void __launch_bounds__(512) k_batch(BatchParams bp) {
     __shared__ BatchItem it;
+    __shared__ unsigned long long s_tile;
     int cur = -1;  // sector whose descriptor is in `it` (same value in every thread)
     const int nr = bp.nrhs;
-    for (unsigned long long tile = blockIdx.x; tile < bp.total_tiles; tile += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(bp.queue, 1ull);
+        __syncthreads();
+        const unsigned long long tile = s_tile;
+        if (tile >= bp.total_tiles) break;
         int k = 0;
         while (k + 1 < bp.n && bp.prefix[k + 1] <= tile) ++k;
         if (k != cur) {  // uniform across the CTA
-            __syncthreads();
             const uint32_t* src = reinterpret_cast<const uint32_t*>(bp.items + k);
             uint32_t* dst = reinterpret_cast<uint32_t*>(&it);
             for (int q = threadIdx.x; q < (int)(sizeof(BatchItem) / 4); q += blockDim.x) dst[q] = src[q];
@@ -76,85 +169,22 @@ __global__ void __launch_bounds__(512) k_batch(BatchParams bp) {
         T* y = reinterpret_cast<T*>(bp.y[k]);
         const unsigned long long r0 = (tile - bp.prefix[k]) * (unsigned long long)bp.rows_per_tile;
         const unsigned long long r1 = min(r0 + (unsigned long long)bp.rows_per_tile, (unsigned long long)S.D);
-        const bool lin2 = S.n_sub == 2;
-        const T* posT = sizeof(T) == 8 ? (const T*)H.pos : (const T*)H.posf;
-        for (unsigned long long i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
-            const uint64_t s = d_unrank(S, S.off, S.str, i);
-            // diagonal: FP64 vectors in FP64; FP32 vectors with FP32 coefficients, compensated
-            T dv;
-            if constexpr (sizeof(T) == 8) {
-                double d = H.C;
-                if (H.lin) {
-                    uint64_t m = s;
-                    while (m) {
-                        int p = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        d += __ldg(H.lin + p);
-                    }
-                }
-                for (int l = 0; l < H.nl; ++l) {
-                    uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
-                    if (H.kpos[l] < 0) {
-                        d += __ldg(H.KA + l) * (double)__popcll(a);
-                    } else {
-                        while (a) {
-                            int p = __ffsll((long long)a) - 1;
-                            a &= a - 1;
-                            d += __ldg(H.pos + H.kpos[l] + p);
-                        }
-                    }
-                }
-                dv = d;
-            } else {
-                RowAcc<float> d;
-                d.init(H.Cf);
-                if (H.linf) {
-                    uint64_t m = s;
-                    while (m) {
-                        int p = __ffsll((long long)m) - 1;
-                        m &= m - 1;
-                        d.add(__ldg(H.linf + p));
-                    }
-                }
-                for (int l = 0; l < H.nl; ++l) {
-                    uint64_t a = (s ^ (s >> H.dist[l])) & H.dmask[l];
-                    if (H.kpos[l] < 0) {
-                        if (a) d.add(__ldg(H.KAf + l) * (float)__popcll(a));
-                    } else {
-                        while (a) {
-                            int p = __ffsll((long long)a) - 1;
-                            a &= a - 1;
-                            d.add(__ldg(H.posf + H.kpos[l] + p));
-                        }
-                    }
-                }
-                dv = d.get();
+        if (WALK) {
+            const unsigned long long w0 = r0 + (unsigned long long)(threadIdx.x >> 5) * 32ull * bp.R;
+            RowWalk<uint64_t> rw;
+            unsigned long long i = w0 + (threadIdx.x & 31);
+            for (int r = 0; r < bp.R && i < r1; ++r, i += 32) {
+                if (r == 0)
+                    walk_start(S, S.off, S.str, i, rw);
+                else
+                    walk_next(S, S.off, S.str, i, rw);
+                batch_row<T>(S, H, x, y, nr, i, rw.s);
             }
-            T xv[kBatchMaxRhs];
-            load_rhs(x + i * nr, nr, xv);
-            RowAcc<T> acc[kBatchMaxRhs];
-#pragma unroll
-            for (int c = 0; c < kBatchMaxRhs; ++c) acc[c].init(c < nr ? dv * xv[c] : (T)0);
-            for (int l = 0; l < H.nl; ++l) {
-                uint64_t o = (s ^ (s >> H.dist[l])) & H.omask[l];
-                const uint64_t pm = 1ull | (1ull << H.dist[l]);
-                const T au = bcf<T>(__ldg(H.KA + kMaxLayers + l), __ldg(H.KAf + kMaxLayers + l));
-                while (o) {
-                    int p = __ffsll((long long)o) - 1;
-                    o &= o - 1;
-                    const uint64_t s2 = s ^ (pm << p);
-                    const uint64_t j = lin2 ? d_rank_lin2(S, s2) : d_rank(S, S.off, S.str, s2);
-                    const T amp = H.apos[l] < 0 ? au : __ldg(posT + H.apos[l] + p);
-                    load_rhs(x + j * nr, nr, xv);
-#pragma unroll
-                    for (int c = 0; c < kBatchMaxRhs; ++c)
-                        if (c < nr) acc[c].add(amp * xv[c]);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < kBatchMaxRhs; ++c)
-                if (c < nr) y[i * nr + c] = acc[c].get();
+        } else {
+            for (unsigned long long i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+                batch_row<T>(S, H, x, y, nr, i, d_unrank(S, S.off, S.str, i));
         }
+        __syncthreads();  // everyone is done with `it` and s_tile before they change
     }
 }
 
@@ -165,12 +195,15 @@ static int sm_count() {
     return sms > 0 ? sms : 1;
 }
 
-// Launch-shape candidates of the autotuner: (threads, CTAs per SM, rows per tile).
+// Candidates of the autotuner: (mapping 0 = rows, 1 = walk; threads; CTAs per SM; rows per
+// tile; rows per lane R of the walk mapping, tile = threads * R).
 struct Shape {
-    int threads, per_sm, tile;
+    int walk, threads, per_sm, tile, R;
 };
-static const Shape kShapes[] = {{128, 8, 2048}, {256, 4, 4096}, {256, 8, 2048}, {512, 2, 8192}, {512, 4, 4096},
-                                {256, 4, 16384}};
+static const Shape kShapes[] = {{0, 128, 8, 2048, 0}, {0, 256, 4, 4096, 0}, {0, 256, 8, 2048, 0},
+                                {0, 512, 2, 8192, 0}, {0, 512, 4, 4096, 0}, {0, 256, 4, 16384, 0},
+                                {1, 128, 8, 1024, 8}, {1, 256, 4, 2048, 8}, {1, 256, 8, 1024, 4},
+                                {1, 512, 2, 8192, 16}, {1, 256, 4, 4096, 16}};
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
 }  // namespace dq
@@ -178,7 +211,7 @@ constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 struct dq_batch {
     int n, nrhs, dtype, shape;
     std::vector<unsigned long long> dims;
-    void* items;  // device array of BatchItem
+    void* items;  // device array of BatchItem, then the tile counter of the work queue
     int device;
 };
 
@@ -191,7 +224,9 @@ static int batch_launch(dq_batch* b, const void* const* x, void* const* y, cudaS
     bp.n = b->n;
     bp.nrhs = b->nrhs;
     bp.rows_per_tile = sh.tile;
+    bp.R = sh.R;
     bp.items = reinterpret_cast<const BatchItem*>(b->items);
+    bp.queue = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(b->items) + sizeof(BatchItem) * b->n);
     unsigned long long t = 0;
     for (int k = 0; k < b->n; ++k) {
         bp.prefix[k] = t;
@@ -203,11 +238,19 @@ static int batch_launch(dq_batch* b, const void* const* x, void* const* y, cudaS
     bp.total_tiles = t;
     unsigned long long cap = (unsigned long long)sm_count() * sh.per_sm;
     unsigned grid = (unsigned)(t < cap ? (t ? t : 1) : cap);
+    cudaMemsetAsync(bp.queue, 0, sizeof(unsigned long long), st);
     const int tslot = timing_start(st);
-    if (b->dtype == DQ_F64)
-        k_batch<double><<<grid, sh.threads, 0, st>>>(bp);
-    else
-        k_batch<float><<<grid, sh.threads, 0, st>>>(bp);
+    if (b->dtype == DQ_F64) {
+        if (sh.walk)
+            k_batch<double, true><<<grid, sh.threads, 0, st>>>(bp);
+        else
+            k_batch<double, false><<<grid, sh.threads, 0, st>>>(bp);
+    } else {
+        if (sh.walk)
+            k_batch<float, true><<<grid, sh.threads, 0, st>>>(bp);
+        else
+            k_batch<float, false><<<grid, sh.threads, 0, st>>>(bp);
+    }
     timing_stop(tslot, st, 1);
     return (int)cudaGetLastError();
 }
@@ -249,7 +292,7 @@ int dq_batch_make(int n, const dq_sector* const* sectors, const dq_terms* const*
         host[k].H = t->q2v;
         b->dims.push_back(s->D);
     }
-    cudaError_t e = cudaMalloc(&b->items, sizeof(BatchItem) * n);
+    cudaError_t e = cudaMalloc(&b->items, sizeof(BatchItem) * n + sizeof(unsigned long long));
     if (e != cudaSuccess) {
         delete b;
         return set_error(DQ_ENOMEM, "cudaMalloc: %s", cudaGetErrorString(e));
@@ -278,6 +321,16 @@ int dq_batch_matvec(dq_batch* b, const void* const* x, void* const* y, void* str
         if (!x[k] || !y[k]) return set_error(DQ_EINVAL, "item %d: NULL vector", k);
     int e = batch_launch(b, x, y, (cudaStream_t)stream, b->shape);
     if (e) return set_error(DQ_ECUDA, "batch launch: %s", cudaGetErrorString((cudaError_t)e));
+    return DQ_OK;
+}
+
+int dq_batch_shape(dq_batch* b, int shape, int* n_shapes) {
+    clear_error();
+    if (!b) return set_error(DQ_EINVAL, "NULL argument");
+    if (n_shapes) *n_shapes = kNumShapes;
+    if (shape < 0) return DQ_OK;
+    if (shape >= kNumShapes) return set_error(DQ_EINVAL, "shape must be in [0, %d)", kNumShapes);
+    b->shape = shape;
     return DQ_OK;
 }
 

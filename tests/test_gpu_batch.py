@@ -30,26 +30,35 @@ def small_items(seed=0):
 
 
 @pytest.mark.parametrize("nrhs", [1, 3, 8])
-def test_batch_small_vs_oracle(nrhs):
+def test_batch_small_vs_oracle_every_mapping(nrhs):
+    """Every candidate of the autotuner (both row mappings, every launch shape) against the
+    oracle; all candidates give bitwise the same y (one thread per row, fixed summation order)."""
     items = small_items(nrhs)
     secs = [b.make_sector(L, 2, N, 0) for L, N, _ in items]
     terms = [b.make_terms(s, t) for s, (_, _, t) in zip(secs, items)]
     rng = np.random.default_rng(100 + nrhs)
     xs = [rng.uniform(-1, 1, (s.dim, nrhs)) for s in secs]
+    oracles = [OracleSector(L, 2, N, partition=s.partition) for s, (L, N, _) in zip(secs, items)]
     for dtype in (torch.float64, torch.float32):
         batch = b.make_batch(secs, terms, nrhs, dtype)
         xt = [torch.from_numpy(x).to(DEV, dtype).contiguous() for x in xs]
-        yt = [torch.empty_like(x) for x in xt]
-        batch.matvec(xt, yt)
-        torch.cuda.synchronize()
-        for s, (L, N, t), x, y in zip(secs, items, xt, yt):
-            o = OracleSector(L, 2, N, partition=s.partition)
-            ref = o_matvec(o, t, x.double().cpu().numpy())
-            got = y.double().cpu().numpy()
-            if dtype == torch.float64:
-                assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+        refs = [o_matvec(o, t, x.double().cpu().numpy()) for o, (_, _, t), x in zip(oracles, items, xt)]
+        first = None
+        for shape in range(batch.n_shapes()):
+            batch.set_shape(shape)
+            yt = [torch.full_like(x, float("nan")) for x in xt]
+            batch.matvec(xt, yt)
+            torch.cuda.synchronize()
+            for ref, y in zip(refs, yt):
+                got = y.double().cpu().numpy()
+                if dtype == torch.float64:
+                    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref)), shape
+                else:
+                    assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref), shape
+            if first is None:
+                first = yt
             else:
-                assert np.linalg.norm(got - ref) <= 1e-5 * np.linalg.norm(ref)
+                assert all(torch.equal(a, c) for a, c in zip(first, yt)), shape
 
 
 @pytest.fixture(scope="module")
@@ -89,7 +98,7 @@ def test_workload4_tune_and_graph_replay(workload4):
     batch.matvec(xt, y0)
     torch.cuda.synchronize()
     choice = batch.tune(xt, [torch.empty_like(x) for x in xt])
-    assert 0 <= choice < 6
+    assert 0 <= choice < batch.n_shapes()
     y1 = [torch.empty_like(x) for x in xt]
     g = torch.cuda.CUDAGraph()
     s = torch.cuda.Stream()
@@ -122,10 +131,15 @@ def test_workload4_largest_sectors_against_oracle_rows(workload4):
     for dtype in (torch.float64, torch.float32):
         batch = b.make_batch(secs, terms, 8, dtype)
         xt = [torch.from_numpy(x).to(DEV, dtype) for x in xs]
-        yt = [torch.empty_like(x) for x in xt]
-        batch.matvec(xt, yt)
-        torch.cuda.synchronize()
-        outs[dtype] = [(xt[k].double().cpu().numpy(), yt[k]) for k in order]
+        ys = []
+        for shape in (1, 7):  # one candidate of each row mapping (block-stride rows, warp walk)
+            batch.set_shape(shape)
+            yt = [torch.empty_like(x) for x in xt]
+            batch.matvec(xt, yt)
+            torch.cuda.synchronize()
+            ys.append([yt[k] for k in order])
+        assert all(torch.equal(a, c) for a, c in zip(*ys))
+        outs[dtype] = [(xt[k].double().cpu().numpy(), ys[0][q]) for q, k in enumerate(order)]
         del batch
     for q, k in enumerate(order):
         w, s = ws[k], secs[k]
