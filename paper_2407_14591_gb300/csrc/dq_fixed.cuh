@@ -188,4 +188,86 @@ inline void launch_col_prepass(const T* x, XT* X, uint64_t rows, int ld, ColScal
     k_col_to_fixed<T, XT><<<grid, bs, 0, st>>>(x, X, n, ld, h);
 }
 
+
+// ------------------------------------------------------------------ one-column prepass -------
+
+// Scratch of the panel products: this header (first 256 bytes), then X = round(x 2^F).
+// Workspace header (first 256 bytes of the scratch area).
+struct WsHeader {
+    int emax;  // largest biased exponent in x
+    int F;     // scale exponent: X = round(x 2^F)
+    int bad;   // x held an Inf or NaN
+};
+
+// Largest biased exponent in x. 16-byte loads when x is 16-byte aligned (the usual case).
+template <typename T>
+__global__ void k_exp_max(const T* __restrict__ x, uint64_t n, WsHeader* h) {
+    using U = typename FBits<T>::U;
+    constexpr int V = 16 / sizeof(T);
+    int m = 0;
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t head = 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+        const uint4* xv = reinterpret_cast<const uint4*>(x);
+        const uint64_t nv = n / V;
+        for (uint64_t i = t0; i < nv; i += step) {
+            const uint4 q = __ldg(xv + i);
+            if (sizeof(T) == 8) {  // the exponent sits in the high word of each double
+                m = max(m, (int)((q.y >> 20) & 0x7ffu));
+                m = max(m, (int)((q.w >> 20) & 0x7ffu));
+            } else {
+                m = max(m, (int)((q.x >> 23) & 0xffu));
+                m = max(m, (int)((q.y >> 23) & 0xffu));
+                m = max(m, (int)((q.z >> 23) & 0xffu));
+                m = max(m, (int)((q.w >> 23) & 0xffu));
+            }
+        }
+        head = nv * V;
+    }
+    for (uint64_t i = head + t0; i < n; i += step) m = max(m, exp_field<T>(reinterpret_cast<const U*>(x)[i]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(&h->emax, m);
+}
+
+// X = round(x 2^F) with F chosen from the largest exponent so that |X| < 2^HEAD. 16-byte loads
+// and stores when x is 16-byte aligned (X always is).
+template <typename T, typename XT>
+__global__ void k_to_fixed(const T* __restrict__ x, XT* __restrict__ X, uint64_t n, WsHeader* h) {
+    using U = typename FBits<T>::U;
+    constexpr int BIAS = FBits<T>::BIAS;
+    const int emax = h->emax;
+    if (emax == FBits<T>::EMASK) {  // Inf or NaN in x
+        if (blockIdx.x == 0 && threadIdx.x == 0) h->bad = 1;
+        return;
+    }
+    // |x| < 2^(emax - BIAS + 1), so X = x 2^F stays below 2^HEAD
+    const int F = XHead<XT>::HEAD - (emax - BIAS + 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) h->F = F;
+    const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, step = (uint64_t)gridDim.x * blockDim.x;
+    uint64_t head = 0;
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0 && sizeof(XT) == sizeof(T)) {
+        // one 16-byte load of x and one 16-byte store of X per step
+        constexpr int V = 16 / sizeof(T);
+        const uint64_t nv = n / V;
+        for (uint64_t i = t0; i < nv; i += step) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(x) + i);
+            uint4 r;
+            if (sizeof(T) == 8) {
+                const unsigned long long v0 =
+                    (unsigned long long)to_fixed<T, XT>((U)(((unsigned long long)q.y << 32) | q.x), F);
+                const unsigned long long v1 =
+                    (unsigned long long)to_fixed<T, XT>((U)(((unsigned long long)q.w << 32) | q.z), F);
+                r = make_uint4((unsigned)v0, (unsigned)(v0 >> 32), (unsigned)v1, (unsigned)(v1 >> 32));
+            } else {
+                r = make_uint4((unsigned)to_fixed<T, XT>((U)q.x, F), (unsigned)to_fixed<T, XT>((U)q.y, F),
+                               (unsigned)to_fixed<T, XT>((U)q.z, F), (unsigned)to_fixed<T, XT>((U)q.w, F));
+            }
+            reinterpret_cast<uint4*>(X)[i] = r;
+        }
+        head = nv * V;
+    }
+    for (uint64_t i = head + t0; i < n; i += step) X[i] = to_fixed<T, XT>(reinterpret_cast<const U*>(x)[i], F);
+}
+
+
 }  // namespace dq

@@ -181,6 +181,45 @@ struct DevTermsCL {
     const long long* M;      // entry coefficient / 2^emin
 };
 
+// Plan of the per-bond panel product (Q = 2, two subsystems, P_1 of at most 13 sites): the
+// structural rank of the panel product (rows sharing a P_0 pattern form one panel) with a
+// coefficient per bond and per site, rounded to one integer grid 2^emin. Bit positions: P_1 holds
+// bits 0 .. L1-1 of the word, P_0 the bits above (s0 = word >> L1).
+constexpr int kPBMaxL1 = 13;
+constexpr int kPBMaxBonds = 64;
+constexpr int kPBMaxGroups = 16;
+struct PanelPB {
+    int L0, L1, N, emin, cmax;
+    uint32_t npanels;
+    const uint32_t* panel_s0;     // P_0 pattern of every panel, canonical order
+    const uint64_t* panel_start;  // first index of every panel
+    const uint16_t* t1rank;       // local index of every P_1 pattern
+    const uint16_t* t1states;     // P_1 patterns grouped by particle number
+    uint32_t t1start[kPBMaxL1 + 2], t1len[kPBMaxL1 + 2];
+    // bonds inside P_1: pair mask (bits lo, hi), hop amplitude and Sz Sz coefficient (device)
+    int n1b;
+    uint32_t p1_lo[kPBMaxBonds], p1_hi[kPBMaxBonds];
+    const long long* p1_A;        // [n1b]
+    const long long* p1_K;        // [n1b]
+    // bonds across the cut, grouped by the P_0 bit a (partner panel s0 ^ a): P_1 bit b and
+    // coefficients; groups with a hop amplitude only (the Sz Sz parts are in xz_*)
+    int nxg;
+    uint32_t xg_abit[kPBMaxGroups];
+    int xg_first[kPBMaxGroups], xg_end[kPBMaxGroups];
+    uint32_t xb_bit[kPBMaxBonds];
+    const long long* xb_A;        // [bonds]
+    int nxz;                       // Sz Sz bonds across the cut: [s_a != s_b] with coefficient K
+    uint32_t xz_abit[kPBMaxBonds], xz_bbit[kPBMaxBonds];
+    const long long* xz_K;
+    const long long* f1;          // [L1]: field of P_1 bit b (coefficient of s_b)
+    const long long* pdiag;       // per panel: constant + P_0 fields + P_0 Sz Sz bonds
+    const long long* p0_A;        // hop amplitude of each P_0 bond (index in the partner entry)
+    // per-panel sources: P_0 partners (start | bond << 48) then cross partners (start | group << 48)
+    const uint32_t* list_off;
+    const uint32_t* list_hdr;     // bits 0-7: P_0 partners, 8-15: cross partners
+    const uint64_t* list;
+};
+
 // Host-side tables kept by a sector.
 struct HostTables {
     std::vector<uint64_t> Dq;  // (L+1) x (nmax_total+1), saturated at UINT64_MAX
@@ -214,6 +253,8 @@ struct dq_terms {
     std::vector<void*> dev_allocs;
     int max_hops;  // upper bound on off-diagonal elements per row
     bool panel_ok = false;     // the panel product applies (see PanelPlan)
+    bool pb_ok = false;        // the per-bond panel product applies (PanelPB)
+    dq::PanelPB pbp;
     bool cluster = false;      // cluster-merged form (App. C), dq_make_cluster_terms
     dq::DevTermsCL clv;
     std::vector<int> cl_sites; // host copy: the sites of each cluster, -1 after the last
@@ -242,6 +283,12 @@ int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y,
 // the same batches for states stored as two uint64 words (low word first)
 int launch_state_at_batch_w(const DevSector& S, const uint64_t* d_index, uint64_t* d_state, uint64_t n, void* stream);
 int launch_index_of_batch_w(const DevSector& S, const uint64_t* d_state, uint64_t* d_index, uint64_t n, void* stream);
+
+// per-bond panel product (dq_panel_pb.cu): plan from the Q = 2 pair list (bit lo, distance) ->
+// (K of [s_lo != s_hi], hop amplitude A), per-position fields and the constant
+int build_panel_pb(const dq_sector* s, double C, const double* lin,
+                   const std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>>& pairs, dq_terms* t);
+int launch_panel_pb(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
 
 // validation shared by the term compilers (dq_terms.cpp): DQ_OK or the error status
 int check_terms(const dq_sector* s, const dq_term* terms, int n_terms);

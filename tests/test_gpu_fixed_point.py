@@ -43,16 +43,18 @@ def test_columns_of_very_different_scale(n_sub):
         assert np.max(np.abs(y[:, c] - ref[:, c])) <= 1e-13 * np.max(np.abs(ref[:, c])), c
 
 
-def test_coefficients_over_sixteen_decades():
-    """Coefficients from 1e-8 to 1e8 share one power-of-two grid; the error stays norm-wise tiny."""
+@pytest.mark.parametrize("n_sub,path", [(2, "panel_pb"), (3, "general")])
+def test_coefficients_over_sixteen_decades(n_sub, path):
+    """Coefficients from 1e-8 to 1e8 share one power-of-two grid; the error stays norm-wise tiny
+    (the per-bond panel kernel and the general kernel)."""
     rng = np.random.default_rng(11)
     L, N = 13, 6
     J = 10.0 ** rng.uniform(-8, 8, L)
     h = 10.0 ** rng.uniform(-8, 8, L) * rng.choice([-1, 1], L)
     terms = wl.heisenberg_terms(wl.chain_bonds(L), J, 0.7) + wl.field_terms(h)
-    s = b.make_sector(L, 2, N, 2)
+    s = b.make_sector(L, 2, N, n_sub)
     t = b.make_terms(s, terms)
-    assert t.path == "general"
+    assert t.path == path
     o = OracleSector(L, 2, N, partition=s.partition)
     x = rng.uniform(-1, 1, o.dim)
     ref = o_matvec(o, terms, x)
@@ -78,7 +80,7 @@ def test_general_nonfinite_input_gives_nan_and_error_word():
     s.check_device()
 
 
-@pytest.mark.parametrize("path", ["panel", "general"])
+@pytest.mark.parametrize("path", ["panel", "panel_pb", "general"])
 def test_graded_column_elementwise_bound(path):
     """One column whose entries span twenty decades (|x_i| = 10^-20u, u ~ U[0, 1], random signs):
     every y_i meets the element-wise bound of the block fixed-point FP64 form,
@@ -92,7 +94,7 @@ def test_graded_column_elementwise_bound(path):
         n_sub = 2
     else:
         terms = xxz_terms(L, rng)
-        n_sub = 3
+        n_sub = 2 if path == "panel_pb" else 3
     s = b.make_sector(L, 2, N, n_sub)
     t = b.make_terms(s, terms)
     assert t.path == path

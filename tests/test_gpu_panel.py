@@ -93,15 +93,19 @@ def test_zero_and_nonfinite_input():
     s.check_device()
 
 
-def test_disorder_falls_back_to_general_kernel():
+def test_disorder_takes_the_per_bond_panel_kernel():
+    """Per-bond couplings leave the class-sum panel kernel for the per-bond one (P_1 of at most 13
+    sites); three subsystems take the general kernel."""
     L = 16
     J = np.random.default_rng(1).uniform(0.5, 1.5, L)
     terms = wl.heisenberg_terms(wl.chain_bonds(L), J)
     s = b.make_sector(L, 2, 8, 2)
-    assert b.make_terms(s, terms).path == "general"
+    assert b.make_terms(s, terms).path == "panel_pb"
     s3 = b.make_sector(L, 2, 8, 3)
     assert b.make_terms(s3, wl.heisenberg_terms(wl.chain_bonds(L), 1.0)).path == "general"
     check(*run_both(L, 8, terms, seed=5, want_panel=False))
+    s30 = b.make_sector(30, 2, 15, 2)  # P_1 of 15 sites: the general kernel
+    assert b.make_terms(s30, wl.heisenberg_terms(wl.chain_bonds(30), np.linspace(0.5, 1.5, 30))).path == "general"
 
 
 def test_repeated_calls_and_two_terms_objects():
@@ -122,14 +126,14 @@ def test_repeated_calls_and_two_terms_objects():
 
 
 def test_timing_hooks_count_and_time_the_main_kernel():
-    """dq_timing_*: three kernels per product on both paths (two prepass kernels and the panel
-    or the fixed-point general kernel), positive times."""
+    """dq_timing_*: three kernels per product on both panel paths (two prepass kernels and the
+    class-sum or the per-bond panel kernel), positive times."""
     s = b.make_sector(20, 2, 10, 2)
     terms = wl.heisenberg_terms(wl.chain_bonds(20), 1.0, 1.0)
     tp = b.make_terms(s, terms)
     assert tp.path == "panel"
-    tg = b.make_terms(s, terms + [("Z", 3, -1, 0.3)])  # a non-uniform field leaves the panel path
-    assert tg.path == "general"
+    tg = b.make_terms(s, terms + [("Z", 3, -1, 0.3)])  # a non-uniform field: the per-bond panel path
+    assert tg.path == "panel_pb"
     x = torch.rand(s.dim, dtype=torch.float64, device=DEV)
     b.matvec(s, tp, x)
     torch.cuda.synchronize()
