@@ -161,8 +161,11 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
  * fields, at most two distinct hop amplitudes and four distinct Sz Sz coefficients, dyadic
  * coefficients), 0 for the general kernels (any Q, partition and nrhs). Both sum exactly in fixed
  * point (see dq_matvec) and compute the same y up to the rounding of the coefficients to their
- * integer grid, which is exact on the panel path. Terms made by dq_make_cluster_terms report 2
- * (the cluster-merged kernel). */
+ * integer grid, which is exact on the panel path. *path = 3 for the per-bond panel kernel, taken
+ * when the panel kernel's conditions on the coefficients fail but the structure fits (Q = 2, two
+ * subsystems, P_1 of at most 13 sites and P_0 of at most 16, at most 64 bonds inside P_1, 64 across
+ * the cut and 200 inside P_0, any coefficient per bond and per site). Terms made by
+ * dq_make_cluster_terms report 2 (the cluster-merged kernel). */
 int dq_terms_path(const dq_terms* t, int* path);
 
 /* Compile terms in the cluster-merged form of App. C instead: the terms are grouped into clusters
