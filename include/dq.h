@@ -294,22 +294,27 @@ void dq_batch_free(dq_batch* b);
  * `dtype`, normalised inside the call, not modified), run up to `steps` steps of
  *   w = H v_k; alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1};
  *   reorth == 1: full re-orthogonalisation by classical Gram-Schmidt against v_0 .. v_k,
- *                w -= V (V^T w), repeated once more when that pass shrank ||w|| below 1/sqrt(2)
- *                of its value before the pass (the Daniel-Gragg-Kaufman-Stewart criterion);
+ *                w -= V (V^T w), repeated once more when ||w|| after that pass is below
+ *                1/sqrt(2) of sqrt(||w||^2 - h_k^2 - h_{k-1}^2) before it, what the three-term
+ *                step alone would leave (the Daniel-Gragg-Kaufman-Stewart criterion);
  *   reorth == 2: the same with the second pass always;
  *   reorth == 0: neither (the plain three-term recurrence);
  *   beta_k = ||w||; v_{k+1} = w / beta_k.
- * Dot products, norms and the vector updates are computed in FP64 whatever `dtype` is; the
- * Lanczos vectors are stored in `dtype`. E0 is the smallest eigenvalue of the tridiagonal matrix
- * T, found on the host by bisection on its Sturm sequence. The call stops early, without error,
- * when beta_k < 1e-14 * ||T||; *steps_done then holds the number of steps taken m. alpha and
+ * With reorth != 0 one pass computes h_j = <v_j, w> for every j <= k (alpha_k = h_k) and the
+ * update w -= sum_j h_j v_j does the three-term step and the re-orthogonalisation at once.
+ * Dot products, norms and vector updates use double-single arithmetic (pairs of floats with
+ * error-free products and sums, about 48 significant bits; partial sums across threads in
+ * FP64) whatever `dtype` is. The basis is stored as float pairs for DQ_F64 and as floats for
+ * DQ_F32; the product reads v_k in `dtype`. E0 is the smallest eigenvalue of the tridiagonal
+ * matrix T, found on the host by bisection on its Sturm sequence. The call stops early, without error,
+ * when beta_k < 1e-12 * ||T||; *steps_done then holds the number of steps taken m. alpha and
  * beta (host, room for `steps` doubles each, may be NULL) receive the recurrence coefficients.
  * psi (device, D elements of `dtype`, may be NULL) receives the Ritz vector of E0,
  * sum_k y_k v_k with y the unit eigenvector of T for E0 (inverse iteration on T, sign chosen so
  * that its largest component is positive); ||H psi - E0 psi|| is the residual of E0.
- * The workspace ((steps+1) vectors of D elements, scratch, 16 bytes of pinned host memory per
- * step) is allocated and freed by the call, and the product's own scratch is kept with the terms
- * (see dq_matvec). The steps run on `stream` without waiting for the host: the call reads each
+ * The workspace ((steps+1) basis vectors of 8 (DQ_F64) or 4 (DQ_F32) bytes per element, three
+ * more vectors, scratch, 16 bytes of pinned host memory per step) is allocated and freed by the
+ * call, and the product's own scratch is kept with the terms (see dq_matvec). The steps run on `stream` without waiting for the host: the call reads each
  * step's coefficients two steps later, so after a breakdown up to two more steps may have run;
  * their results are dropped. Synchronous: returns when E0 (and psi) are known. Errors: DQ_EINVAL
  * (NULL or out-of-range arguments, steps outside [1, 4096], reorth outside [0, 2], a zero or

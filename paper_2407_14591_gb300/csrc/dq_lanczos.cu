@@ -1,27 +1,37 @@
 // Lanczos driver for the ground-state energy (Sec. 4.4; App. D calls a native Lanczos): the
-// only use of H is the matrix-free product. Vectors live on the device in the caller's dtype;
-// every dot product and norm accumulates in FP64 with a fixed reduction order (the result does
-// not depend on timing). The tridiagonal matrix T is solved on the host by bisection on its
-// Sturm sequence, and the Ritz vector's coefficients by inverse iteration (own
+// only use of H is the matrix-free product. The tridiagonal matrix T is solved on the host by
+// bisection on its Sturm sequence, and the Ritz vector's coefficients by inverse iteration (own
 // implementations).
 //
 // One step is two launches: the product w = H v_k, then one cooperative kernel (k_lz_step, all
 // blocks resident, grid-wide barriers between its phases) that does the rest on the device:
-//   alpha_k = <v_k, w>;  w -= alpha_k v_k + beta_{k-1} v_{k-1}      (rho0 = ||w||)
-//   with re-orthogonalisation, classical Gram-Schmidt against V = [v_0 .. v_k]:
-//     h = V^T w; w -= V h                                           (rho1 = ||w||)
-//     a second pass only if rho1 < rho0 / sqrt(2) (the DGKS criterion; always with reorth = 2)
-//   beta_k = ||w||; v_{k+1} = w / beta_k
-// Every block reduces the partial sums itself in the same fixed order, so all blocks hold the
-// same coefficients without another barrier. alpha_k and beta_k^2 go to device arrays and to
-// mapped pinned host memory. The host reads step k's values only after it has queued step k+2,
-// so the GPU never waits for the host; a breakdown found late only costs the steps already
-// queued, whose results are dropped.
-// Arithmetic: FP64 for dot products, norms, the three-term step and (FP64 vectors) the
-// Gram-Schmidt updates; FP32 vectors are widened to FP64 with integer bit operations (exact)
-// and take their Gram-Schmidt updates, whose coefficients are at the level of the vectors' own
-// rounding, as FP32 multiply-adds. The FP64 multiply-adds of the passes over V (2 D (k+1) per
-// step) bound a step on this GPU, whose FP64 rate is a small fraction of its integer rate.
+//   alpha_k = <v_k, w>;  r = w - alpha_k v_k - beta_{k-1} v_{k-1}         (rho0 = ||r||^2)
+//   with re-orthogonalisation, classical Gram-Schmidt of r against V = [v_0 .. v_k]:
+//     h = V^T r; r -= V h; alpha_k += h_k                                  (rho1 = ||r||^2)
+//     a second pass only if rho1 < rho0 / 2 (the DGKS criterion; always with reorth = 2)
+//   beta_k = ||r||; v_{k+1} = r / beta_k.
+// The three-term remainder is formed inside the first tile of the projection pass (from w, v_k
+// and v_{k-1}), so it costs no pass of its own. Gram-Schmidt acts on that remainder, not on w:
+// applied to w itself, one pass would multiply the basis's loss of orthogonality by
+// ||w|| / beta_k at every step.
+// Partial sums are reduced in a fixed order (the result does not depend on timing); every block
+// derives the same coefficients. alpha_k and beta_k^2 go to device arrays and to mapped pinned
+// host memory. The host reads step k's values only after it has queued step k+2, so the GPU
+// never waits for the host; a breakdown found late only costs the steps already queued, whose
+// results are dropped.
+//
+// Arithmetic. FP64 runs on this GPU at a small fraction of its FP32 rate, and a pass over V does
+// (k + 1) multiply-adds per element, so the passes over V use double-single arithmetic: a value
+// is an unevaluated sum of two floats (hi, lo). Products are error-free in their leading part
+// (p = a*b and its exact error fma(a, b, -p)), sums use Knuth's TwoSum, and the compensation
+// terms are summed in FP32 and folded into a second float pair every kFlush terms: the dot
+// product scheme Dot2 of Ogita, Rump and Oishi (SIAM J. Sci. Comput. 26, 2005), which returns
+// the result as if computed with 48-bit significands and rounded once. Block partials are
+// combined in FP64. The basis of FP64 vectors is stored as float pairs (48 significant bits);
+// the vector the next product reads is their sum in FP64. FP32 vectors are stored as floats and
+// the residual r is kept as a float pair inside a step. Conversions between double and float
+// pairs use integer bit operations (no FP64 instruction).
+
 #include <cmath>
 #include <cstdint>
 #include <vector>
@@ -34,17 +44,9 @@ namespace dq {
 
 constexpr int kRedThreads = 256;
 constexpr int kDotTile = 16;  // basis vectors per pass of the blocked dot kernel
-
-// Device scalars of the driver (one array of doubles in the workspace).
-enum : int {
-    kAlpha = 0,    // alpha_k
-    kRho0 = 1,     // ||w||^2 after the three-term step
-    kRho1 = 2,     // ||w||^2 after the first Gram-Schmidt pass
-    kBeta2 = 3,    // ||w||^2 at the end of the step: beta_k^2
-    kPass2 = 4,    // 1.0 if the second pass runs
-    kV0 = 5,       // ||v0||^2
-    kNScal = 8,
-};
+constexpr int kLzThreads = 512;  // threads of a step-kernel block
+constexpr int kLzTile = 8;       // basis vectors per tile of the projection pass (one warp each)
+constexpr int kFlush = 32;       // terms summed into a float pair before it is folded into the next
 
 // Sum of v over the block; the total is returned in thread 0 only (sh: 32 doubles).
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -133,10 +135,11 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_dots(const T* __restrict__ V
 }
 
 // Exact widening of a float to double with integer operations (the hardware conversion runs on
-// the FP64 pipe); zero, subnormals, Inf and NaN take the hardware path.
+// the FP64 pipe); subnormals, Inf and NaN take the hardware path.
 __device__ __forceinline__ double widen(float f) {
     const unsigned u = __float_as_uint(f);
     const unsigned e = (u >> 23) & 0xffu;
+    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
     if (e == 0u || e == 0xffu) return (double)f;
     const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
                                     ((unsigned long long)(e + 896u) << 52) |
@@ -195,17 +198,176 @@ __device__ __forceinline__ double reduce_all(const double* part, int nb, double*
     return acc;
 }
 
+// ---- double-single arithmetic ---------------------------------------------------------------
+// A pair (S, C) stands for S + C. Every operation uses the _rn intrinsics, which the compiler
+// never contracts into fused multiply-adds, so each error-free transformation stays exact.
+
+// (S, C) += p: TwoSum gives S + p = s + err exactly; err joins the compensation C.
+__device__ __forceinline__ void ff_add(float& S, float& C, float p) {
+    const float s = __fadd_rn(S, p);
+    const float bp = __fsub_rn(s, S);
+    const float err = __fadd_rn(__fsub_rn(S, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    S = s;
+    C = __fadd_rn(C, err);
+}
+
+// (S, C) += (s, c)
+__device__ __forceinline__ void ff_fold(float& S, float& C, float s, float c) {
+    ff_add(S, C, s);
+    C = __fadd_rn(C, c);
+}
+
+// (S, C) += (ah + al)(bh + bl): ah*bh = p + e exactly (e by a fused multiply-add), the cross
+// terms join e; al*bl lies below the pair's precision and is dropped.
+__device__ __forceinline__ void ff_mac(float& S, float& C, float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    ff_add(S, C, p);
+    C = __fadd_rn(C, e);
+}
+
+// (S, C) += (h + l)^2
+__device__ __forceinline__ void ff_sq(float& S, float& C, float h, float l) {
+    const float p = __fmul_rn(h, h);
+    float e = __fmaf_rn(h, h, -p);
+    e = __fmaf_rn(__fadd_rn(h, h), l, e);
+    ff_add(S, C, p);
+    C = __fadd_rn(C, e);
+}
+
+// (rh, rl) = (ah + al) - (bh + bl), renormalised so that |rl| <= ulp(rh) / 2.
+__device__ __forceinline__ void ff_sub(float ah, float al, float bh, float bl, float& rh, float& rl) {
+    const float s = __fsub_rn(ah, bh);
+    const float bp = __fsub_rn(s, ah);
+    const float err = __fsub_rn(__fsub_rn(ah, __fsub_rn(s, bp)), __fadd_rn(bh, bp));  // s + err = ah - bh
+    const float t = __fadd_rn(err, __fsub_rn(al, bl));
+    rh = __fadd_rn(s, t);
+    rl = __fsub_rn(t, __fsub_rn(rh, s));
+}
+
+// (vh, vl) = (rh + rl)(sh + sl), renormalised.
+__device__ __forceinline__ void ff_mul(float rh, float rl, float sh, float sl, float& vh, float& vl) {
+    const float p = __fmul_rn(rh, sh);
+    float e = __fmaf_rn(rh, sh, -p);
+    e = __fmaf_rn(rh, sl, e);
+    e = __fmaf_rn(rl, sh, e);
+    vh = __fadd_rn(p, e);
+    vl = __fsub_rn(e, __fsub_rn(vh, p));
+}
+
+// x = hi + lo with hi = x cut to 24 significant bits and lo the remainder rounded to FP32 (48
+// significant bits together), by integer operations when both are normal floats
+// (2^-74 <= |x| < 2^128); other x (zero, tiny, huge, Inf, NaN) take the hardware conversions.
+__device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
+    if (e >= 949u && e <= 1150u) {
+        const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+        hi = __uint_as_float(sign | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
+        const float scale = __uint_as_float(sign | ((e - 948u) << 23));  // +-2^(e - 1075)
+        lo = __fmul_rn(__uint2float_rn((unsigned)b & 0x1fffffffu), scale);
+    } else {
+        hi = __double2float_rn(x);
+        lo = __double2float_rn(x - (double)hi);
+    }
+}
+
+// The basis: FP64 vectors keep each element as a float pair (hi, lo), FP32 vectors as a float.
+template <typename T>
+struct Basis;
+template <>
+struct Basis<double> {
+    using S = float2;
+};
+template <>
+struct Basis<float> {
+    using S = float;
+};
+__device__ __forceinline__ void ld_basis(const float2* p, float& h, float& l) {
+    const float2 v = __ldg(p);
+    h = v.x;
+    l = v.y;
+}
+__device__ __forceinline__ void ld_basis(const float* p, float& h, float& l) {
+    h = __ldg(p);
+    l = 0.f;
+}
+// Store the renormalised pair (h, l) as a basis element; FP64 vectors also store its value in
+// FP64 (the next product's input), FP32 vectors store h + l rounded (itself that input).
+__device__ __forceinline__ void st_basis(float2* p, double* x, float h, float l) {
+    *p = make_float2(h, l);
+    *x = widen(h) + widen(l);
+}
+__device__ __forceinline__ void st_basis(float* p, double*, float h, float l) { *p = __fadd_rn(h, l); }
+
+// The product's output as a pair.
+__device__ __forceinline__ void ld_pair(const double* p, float& h, float& l) { split_f64(__ldg(p), h, l); }
+__device__ __forceinline__ void ld_pair(const float* p, float& h, float& l) {
+    h = __ldg(p);
+    l = 0.f;
+}
+__device__ __forceinline__ void st_value(double* p, float h, float l) { *p = widen(h) + widen(l); }
+__device__ __forceinline__ void st_value(float* p, float h, float l) { *p = __fadd_rn(h, l); }
+
+// Sum of the pairs (S, C) of the block, in FP64 in thread 0 (shp: 32 pairs).
+__device__ __forceinline__ double block_pair_sum(float S, float C, float2* shp) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_down_sync(0xffffffffu, S, o), co = __shfl_down_sync(0xffffffffu, C, o);
+        ff_fold(S, C, so, co);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) shp[wid] = make_float2(S, C);
+    __syncthreads();
+    double r = 0.0;
+    if (wid == 0) {
+        float s = 0.f, c = 0.f;
+        if (lane < (int)(blockDim.x >> 5)) {
+            s = shp[lane].x;
+            c = shp[lane].y;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float so = __shfl_down_sync(0xffffffffu, s, o), co = __shfl_down_sync(0xffffffffu, c, o);
+            ff_fold(s, c, so, co);
+        }
+        r = widen(s) + widen(c);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Sum of the FP64 block partials part[0 .. nb) in a fixed order, in float pairs, returned to
+// every thread of the block; every block gets the same value.
+__device__ __forceinline__ double lz_reduce_all(const double* part, int nb, float2* shp, double* bc) {
+    float s = 0.f, c = 0.f;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        float h, l;
+        split_f64(__ldcg(part + b), h, l);
+        ff_fold(s, c, h, l);
+    }
+    const double v = block_pair_sum(s, c, shp);
+    if (threadIdx.x == 0) *bc = v;
+    __syncthreads();
+    const double r = *bc;
+    __syncthreads();
+    return r;
+}
+
 template <typename T>
 struct LzStep {
-    const T* V;       // v_0 .. v_k, stride ldv
+    using S = typename Basis<T>::S;
+    const S* V;       // basis v_0 .. v_k, stride ldv
     size_t ldv;
     int k;            // step index
-    T* w;             // H v_k on entry; the new residual on exit
-    T* vnext;         // v_{k+1} (NULL at the last step)
+    const T* w;       // H v_k (the product's output)
+    float2* r;        // the residual as float pairs
+    S* vnext;         // v_{k+1} in the basis (NULL at the last step)
+    double* xnext;    // v_{k+1} in FP64 for the next product (FP64 vectors)
     uint64_t n;
     int reorth;       // 0, 1 (DGKS second pass), 2 (second pass always)
-    double* part;     // per-block partial sums, gridDim.x * (2 (k+1) + 8) doubles
-    double* h;        // projection coefficients, k+1 doubles
+    double* part;     // per-block partial sums, gridDim.x * (k + 5) doubles
+    double* h;        // projection coefficients, k + 1 doubles
     double* alpha;    // alpha_j, beta_j^2 of every step (device)
     double* beta2;
     volatile double* host;  // mapped pinned host memory: alpha_k, beta_k^2 at [2k], [2k+1]
@@ -213,139 +375,334 @@ struct LzStep {
     int* fail;        // barrier timeout
 };
 
-// h = V^T w over j <= k (partials per block and vector, then block b reduces the vectors
-// j = b, b + nb, ... in block order), followed by w -= V h and the block partials of ||w||^2.
+
+// alpha pass: the block partial of <v_k, w> into pa[b]; w is also stored as float pairs in r.
+// Two elements per iteration, so that each thread has four loads in flight.
 template <typename T>
-__device__ __forceinline__ bool lz_gram_schmidt(const LzStep<T>& a, double* pd, double* pn, double* hs,
-                                                double* red) {
-    __shared__ double sh[kDotTile][kRedThreads / 32];
-    const int kk = a.k + 1, lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-    for (int j0 = 0; j0 < kk; j0 += kDotTile) {
-        const int nj = kk - j0 < kDotTile ? kk - j0 : kDotTile;
-        double acc[kDotTile];
+__device__ bool lz_alpha(const LzStep<T>& a, const typename Basis<T>::S* vk, double* pa, float2* shp) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    int cnt = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += 2 * stride) {
+        const uint64_t i2 = i + stride;
+        const bool two = i2 < a.n;
+        float wh, wl, vh, vl, wh2 = 0.f, wl2 = 0.f, vh2 = 0.f, vl2 = 0.f;
+        ld_pair(a.w + i, wh, wl);
+        ld_basis(vk + i, vh, vl);
+        if (two) {
+            ld_pair(a.w + i2, wh2, wl2);
+            ld_basis(vk + i2, vh2, vl2);
+        }
+        a.r[i] = make_float2(wh, wl);
+        ff_mac(s1, c1, vh, vl, wh, wl);
+        if (two) {
+            a.r[i2] = make_float2(wh2, wl2);
+            ff_mac(s1, c1, vh2, vl2, wh2, wl2);
+        }
+        if (++cnt == kFlush / 2) {
+            cnt = 0;
+            ff_fold(s2, c2, s1, c1);
+            s1 = c1 = 0.f;
+        }
+    }
+    ff_fold(s2, c2, s1, c1);
+    const double v = block_pair_sum(s2, c2, shp);
+    if (threadIdx.x == 0) pa[blockIdx.x] = v;
+    return grid_sync(a.bar, a.fail);
+}
+
+// The block's slab of elements for the projection: [lo, hi), contiguous, a multiple of 32 long.
+__device__ __forceinline__ void lz_slab(uint64_t n, uint64_t& lo, uint64_t& hi) {
+    const uint64_t per = ((n + gridDim.x - 1) / gridDim.x + 31) & ~(uint64_t)31;
+    lo = per * blockIdx.x;
+    hi = lo + per < n ? lo + per : n;
+    if (lo > n) lo = n;
+}
+
+// Projection pass: block partials pd[b * (k + 1) + j] of h_j = <v_j, r> for j <= k. Block b owns
+// a contiguous slab of elements; its warps share the basis vectors in tiles of kLzTile (warp w
+// takes tiles w, w + 8, ...), each lane summing its strided elements of the slab in float pairs
+// (folded every kFlush elements into a second pair kept in shared memory, fls, so that four
+// blocks fit on an SM without register spills), and a shuffle tree gives the warp's partial
+// for each vector of the tile. No block barrier inside the tiles, so they proceed side by side;
+// with fewer tiles than warps, several warps share a tile (wp: their sums). first: before the tiles, the block replaces r (holding w) on its slab by the
+// three-term remainder r - alpha v_k - beta v_{k-1} (ab = alpha and beta as float pairs) and puts
+// ||r||^2 into pw[b].
+template <typename T>
+__device__ bool lz_project(const LzStep<T>& a, float4 ab, bool first, double* pd, double* pw, float2* shp,
+                           float2* wp, float2* fls) {
+    using S = typename Basis<T>::S;
+    const int nj = a.k + 1;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint64_t lo, hi;
+    lz_slab(a.n, lo, hi);
+    if (first) {
+        const S* vk = a.V + (size_t)a.k * a.ldv;
+        const S* vp = a.k ? vk - a.ldv : nullptr;
+        float ns = 0.f, nc = 0.f, ns2 = 0.f, nc2 = 0.f;
+        int cnt = 0;
+        for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const float2 rv = a.r[i];
+            float ts = 0.f, tc = 0.f, uh, ul, wh, wl;
+            ld_basis(vk + i, uh, ul);
+            ff_mac(ts, tc, uh, ul, ab.x, ab.y);
+            if (vp) {
+                ld_basis(vp + i, uh, ul);
+                ff_mac(ts, tc, uh, ul, ab.z, ab.w);
+            }
+            ff_sub(rv.x, rv.y, ts, tc, wh, wl);
+            a.r[i] = make_float2(wh, wl);
+            ff_sq(ns, nc, wh, wl);
+            if (++cnt == kFlush) {
+                cnt = 0;
+                ff_fold(ns2, nc2, ns, nc);
+                ns = nc = 0.f;
+            }
+        }
+        ff_fold(ns2, nc2, ns, nc);
+        const double v = block_pair_sum(ns2, nc2, shp);  // also orders the writes to r above
+        if (threadIdx.x == 0) pw[blockIdx.x] = v;
+    }
+    // P warps per tile when there are fewer tiles than warps (each takes every P-th 32-element
+    // chunk of the slab; their sums are combined through shared memory in part order)
+    const int ntile = (nj + kLzTile - 1) / kLzTile;
+    const int P = ntile >= nw ? 1 : nw / ntile;
+    const int part = wid % P;
+    for (int t0 = (wid / P) * kLzTile; t0 < nj; t0 += (nw / P) * kLzTile) {
+        const int nt = nj - t0 < kLzTile ? nj - t0 : kLzTile;
+        const S* Vb = a.V + (size_t)t0 * a.ldv;
+        float s1[kLzTile], c1[kLzTile];
+        float2* fl = fls + wid * kLzTile * 32 + lane;  // this lane's second-level pairs
 #pragma unroll
-        for (int q = 0; q < kDotTile; ++q) acc[q] = 0.0;
-        const T* Vb = a.V + (size_t)j0 * a.ldv;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step) {
-            const double wi = widen(a.w[i]);
+        for (int q = 0; q < kLzTile; ++q) {
+            s1[q] = c1[q] = 0.f;
+            fl[q * 32] = make_float2(0.f, 0.f);
+        }
+        int cnt = 0;
+        for (uint64_t i = lo + 32 * part + lane; i < hi; i += 32 * P) {
+            const float2 rv = a.r[i];
+            float vh[kLzTile], vl[kLzTile];
 #pragma unroll
-            for (int q = 0; q < kDotTile; ++q)
-                if (q < nj) acc[q] += widen(__ldg(Vb + (size_t)q * a.ldv + i)) * wi;
+            for (int q = 0; q < kLzTile; ++q) {
+                vh[q] = vl[q] = 0.f;
+                if (q < nt) ld_basis(Vb + (size_t)q * a.ldv + i, vh[q], vl[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < kLzTile; ++q) ff_mac(s1[q], c1[q], vh[q], vl[q], rv.x, rv.y);
+            if (++cnt == kFlush) {
+                cnt = 0;
+#pragma unroll
+                for (int q = 0; q < kLzTile; ++q) {
+                    float2 m = fl[q * 32];
+                    ff_fold(m.x, m.y, s1[q], c1[q]);
+                    fl[q * 32] = m;
+                    s1[q] = c1[q] = 0.f;
+                }
+            }
         }
 #pragma unroll
-        for (int q = 0; q < kDotTile; ++q) {
-            double v = acc[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) sh[q][wid] = v;
+        for (int q = 0; q < kLzTile; ++q) {
+            float2 m = fl[q * 32];
+            ff_fold(m.x, m.y, s1[q], c1[q]);
+            for (int o = 16; o > 0; o >>= 1) {
+                const float so = __shfl_down_sync(0xffffffffu, m.x, o);
+                const float co = __shfl_down_sync(0xffffffffu, m.y, o);
+                ff_fold(m.x, m.y, so, co);
+            }
+            if (lane == 0 && q < nt) {
+                if (P == 1)
+                    pd[(size_t)blockIdx.x * nj + t0 + q] = widen(m.x) + widen(m.y);
+                else
+                    wp[wid * kLzTile + q] = m;
+            }
+        }
+    }
+    if (P > 1) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < nj; j += blockDim.x) {
+            const int w0 = (j / kLzTile) * P, q = j % kLzTile;
+            float sq = 0.f, cq = 0.f;
+            for (int p = 0; p < P; ++p) ff_fold(sq, cq, wp[(w0 + p) * kLzTile + q].x, wp[(w0 + p) * kLzTile + q].y);
+            pd[(size_t)blockIdx.x * nj + j] = widen(sq) + widen(cq);
+        }
+    }
+    return grid_sync(a.bar, a.fail);
+}
+
+// h_j for j <= k from the block partials: one warp per vector sums the blocks' partials in float
+// pairs in a fixed order (lane l takes blocks l, l + 32, ..., then a shuffle tree). With at most
+// as many vectors as a block has warps every block does this for all of them into hd (no grid
+// barrier); otherwise the warps of the grid share the vectors, write a.h, and after a barrier
+// each block copies a.h into hd. Either way every block holds the same values.
+template <typename T>
+__device__ bool lz_reduce(const LzStep<T>& a, const double* pd, double* hd) {
+    const int nj = a.k + 1, nb = gridDim.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    auto column = [&](int j) {
+        float s = 0.f, c = 0.f;
+        for (int b = lane; b < nb; b += 32) {
+            float h, l;
+            split_f64(__ldcg(pd + (size_t)b * nj + j), h, l);
+            ff_fold(s, c, h, l);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float so = __shfl_down_sync(0xffffffffu, s, o), co = __shfl_down_sync(0xffffffffu, c, o);
+            ff_fold(s, c, so, co);
+        }
+        return widen(s) + widen(c);
+    };
+    if (nj <= nw) {
+        if (wid < nj) {
+            const double v = column(wid);
+            if (lane == 0) hd[wid] = v;
         }
         __syncthreads();
-        if (threadIdx.x < nj) {
-            double sum = 0.0;
-            for (int r = 0; r < kRedThreads / 32; ++r) sum += sh[threadIdx.x][r];
-            pd[(size_t)blockIdx.x * kk + j0 + threadIdx.x] = sum;
-        }
-        __syncthreads();
+        return true;
+    }
+    for (int j = blockIdx.x * nw + wid; j < nj; j += nb * nw) {
+        const double v = column(j);
+        if (lane == 0) a.h[j] = v;
     }
     if (!grid_sync(a.bar, a.fail)) return false;
-    for (int j = blockIdx.x; j < kk; j += gridDim.x) {
-        double acc = 0.0;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) acc += __ldcg(pd + (size_t)b * kk + j);
-        acc = block_sum(acc, red);
-        if (threadIdx.x == 0) a.h[j] = acc;
-    }
-    if (!grid_sync(a.bar, a.fail)) return false;
-    for (int q = threadIdx.x; q < kk; q += blockDim.x) hs[q] = __ldcg(a.h + q);
+    for (int j = threadIdx.x; j < nj; j += blockDim.x) hd[j] = __ldcg(a.h + j);
     __syncthreads();
-    double nacc = 0.0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step) {
-        T r;
-        if constexpr (sizeof(T) == 8) {
-            double acc = a.w[i];
-            int j = 0;
-            for (; j + 8 <= kk; j += 8) {
-                double v[8];
+    return true;
+}
+
+// Update pass: r -= sum_{j in [u0, k]} c_j v_j over the thread's elements (c as float pairs in
+// cf), ten (float pairs) or sixteen (floats) basis loads in flight per round and two
+// independent pair sums over j, folded into one every 4 kFlush terms; then the block partial of
+// ||r||^2 into pr[b].
+template <typename T>
+__device__ bool lz_update(const LzStep<T>& a, int u0, const float2* cf, double* pr, float2* shp) {
+    constexpr int kG = sizeof(typename Basis<T>::S) == 8 ? 10 : 16;  // loads per round (registers)
+    const int kk = a.k + 1;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    float ns = 0.f, nc = 0.f, ns2 = 0.f, nc2 = 0.f;
+    int cnt = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += stride) {
+        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, fs = 0.f, fc = 0.f;
+        for (int j0 = u0; j0 < kk; j0 += 4 * kFlush) {
+            const int je = kk - j0 < 4 * kFlush ? kk : j0 + 4 * kFlush;
+            for (int j = j0; j < je; j += kG) {  // kG loads in flight; past je they are zeros
+                float vh[kG], vl[kG];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = __ldg(a.V + (size_t)(j + q) * a.ldv + i);
+                for (int q = 0; q < kG; ++q) {
+                    vh[q] = vl[q] = 0.f;
+                    if (j + q < je) ld_basis(a.V + (size_t)(j + q) * a.ldv + i, vh[q], vl[q]);
+                }
+                // a padded term multiplies a zero by the last (finite) coefficient
 #pragma unroll
-                for (int q = 0; q < 8; ++q) acc -= hs[j + q] * v[q];
+                for (int q = 0; q < kG; q += 2) {
+                    const float2 ca = cf[j + q < je ? j + q : je - 1], cb = cf[j + q + 1 < je ? j + q + 1 : je - 1];
+                    ff_mac(s0, c0, vh[q], vl[q], ca.x, ca.y);
+                    ff_mac(s1, c1, vh[q + 1], vl[q + 1], cb.x, cb.y);
+                }
             }
-            for (; j < kk; ++j) acc -= hs[j] * __ldg(a.V + (size_t)j * a.ldv + i);
-            r = acc;
-        } else {
-            float corr = 0.f;
-            int j = 0;
-            for (; j + 8 <= kk; j += 8) {
-                float v[8];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) v[q] = __ldg(a.V + (size_t)(j + q) * a.ldv + i);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) corr = fmaf((float)hs[j + q], v[q], corr);
-            }
-            for (; j < kk; ++j) corr = fmaf((float)hs[j], __ldg(a.V + (size_t)j * a.ldv + i), corr);
-            r = a.w[i] - corr;
+            ff_fold(fs, fc, s0, c0);
+            ff_fold(fs, fc, s1, c1);
+            s0 = c0 = s1 = c1 = 0.f;
         }
-        a.w[i] = r;
-        const double rd = widen(r);
-        nacc += rd * rd;
+        const float2 rv = a.r[i];
+        float rh, rl;
+        ff_sub(rv.x, rv.y, fs, fc, rh, rl);
+        a.r[i] = make_float2(rh, rl);
+        ff_sq(ns, nc, rh, rl);
+        if (++cnt == kFlush) {
+            cnt = 0;
+            ff_fold(ns2, nc2, ns, nc);
+            ns = nc = 0.f;
+        }
     }
-    nacc = block_sum(nacc, red);
-    if (threadIdx.x == 0) pn[blockIdx.x] = nacc;
+    ff_fold(ns2, nc2, ns, nc);
+    const double v = block_pair_sum(ns2, nc2, shp);
+    if (threadIdx.x == 0) pr[blockIdx.x] = v;
     return grid_sync(a.bar, a.fail);
 }
 
 // One Lanczos step after the product (see the file comment). Cooperative launch; dynamic shared
-// memory: k + 1 doubles (the projection coefficients).
+// memory: k + 1 doubles (the coefficients) and k + 1 float pairs (the coefficients split).
 template <typename T>
-__global__ void __launch_bounds__(kRedThreads) k_lz_step(LzStep<T> a) {
-    extern __shared__ double hs[];
-    __shared__ double red[33];
-    const int nb = gridDim.x;
-    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
-    double* p_alpha = a.part;
-    double* p_rho0 = a.part + nb;
-    double* p_rho1 = a.part + 2 * nb;
-    double* p_rho2 = a.part + 3 * nb;
-    double* p_dots = a.part + 4 * nb;  // nb * kk
-    const T* vk = a.V + (size_t)a.k * a.ldv;
-    const T* vp = a.k ? a.V + (size_t)(a.k - 1) * a.ldv : nullptr;
-    // alpha_k = <v_k, w>
-    double acc = 0.0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step)
-        acc += widen(__ldg(vk + i)) * widen(a.w[i]);
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) p_alpha[blockIdx.x] = acc;
-    if (!grid_sync(a.bar, a.fail)) return;
-    const double al = reduce_all(p_alpha, nb, red);
-    const double be = vp ? sqrt(__ldcg(a.beta2 + a.k - 1)) : 0.0;
-    // three-term step, rho0^2
-    acc = 0.0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step) {
-        double r = widen(a.w[i]) - al * widen(__ldg(vk + i));
-        if (vp) r -= be * widen(__ldg(vp + i));
-        const T rt = (T)r;
-        a.w[i] = rt;
-        const double rd = widen(rt);
-        acc += rd * rd;
-    }
-    acc = block_sum(acc, red);
-    if (threadIdx.x == 0) p_rho0[blockIdx.x] = acc;
-    if (!grid_sync(a.bar, a.fail)) return;
-    double b2 = reduce_all(p_rho0, nb, red);
-    if (a.reorth) {
-        const double rho0 = b2;
-        if (!lz_gram_schmidt(a, p_dots, p_rho1, hs, red)) return;
-        b2 = reduce_all(p_rho1, nb, red);
+__global__ void __launch_bounds__(kLzThreads, 2) k_lz_step(LzStep<T> a) {
+    extern __shared__ __align__(16) unsigned char lz_smem[];
+    double* hd = reinterpret_cast<double*>(lz_smem);
+    float2* cf = reinterpret_cast<float2*>(hd + a.k + 1);
+    __shared__ float2 shp[32];
+    __shared__ double bcast;
+    __shared__ float2 scale;
+    __shared__ float2 wp[kLzThreads / 32 * kLzTile];        // the projection's per-warp sums
+    __shared__ float2 fls[kLzThreads / 32 * kLzTile * 32];  // its per-lane second-level pairs
+    const int nb = gridDim.x, kk = a.k + 1;
+    double* pa = a.part;   // <v_k, w>
+    double* pw = pa + nb;  // ||r||^2 after the three-term step
+    double* pr1 = pw + nb; // after the first Gram-Schmidt pass (or the three-term update)
+    double* pr2 = pr1 + nb;
+    double* pd = pr2 + nb; // projection partials, nb * (k + 1)
+    if (!lz_alpha(a, a.V + (size_t)a.k * a.ldv, pa, shp)) return;
+    double al = lz_reduce_all(pa, nb, shp, &bcast);
+    const double be = a.k ? sqrt(__ldcg(a.beta2 + a.k - 1)) : 0.0;
+    double b2;
+    if (!a.reorth) {  // r -= alpha_k v_k + beta_{k-1} v_{k-1}
+        if (threadIdx.x < 2 && (threadIdx.x == 0 || a.k)) {
+            float h, l;
+            split_f64(threadIdx.x ? be : al, h, l);
+            cf[a.k - threadIdx.x] = make_float2(h, l);
+        }
+        __syncthreads();
+        if (!lz_update(a, a.k ? a.k - 1 : 0, cf, pr1, shp)) return;
+        b2 = lz_reduce_all(pr1, nb, shp, &bcast);
+    } else {
+        float4 ab;
+        split_f64(al, ab.x, ab.y);
+        split_f64(be, ab.z, ab.w);
+        if (!lz_project(a, ab, true, pd, pw, shp, wp, fls)) return;
+        if (!lz_reduce(a, pd, hd)) return;
+        al += hd[a.k];
+        for (int j = threadIdx.x; j < kk; j += blockDim.x) {
+            float h, l;
+            split_f64(hd[j], h, l);
+            cf[j] = make_float2(h, l);
+        }
+        __syncthreads();
+        if (!lz_update(a, 0, cf, pr1, shp)) return;
+        b2 = lz_reduce_all(pr1, nb, shp, &bcast);
+        const double rho0 = lz_reduce_all(pw, nb, shp, &bcast);
         if (a.reorth == 2 || b2 < 0.5 * rho0) {
-            if (!lz_gram_schmidt(a, p_dots, p_rho2, hs, red)) return;
-            b2 = reduce_all(p_rho2, nb, red);
+            if (!lz_project(a, ab, false, pd, nullptr, shp, wp, fls)) return;
+            if (!lz_reduce(a, pd, hd)) return;
+            al += hd[a.k];
+            for (int j = threadIdx.x; j < kk; j += blockDim.x) {
+                float h, l;
+                split_f64(hd[j], h, l);
+                cf[j] = make_float2(h, l);
+            }
+            __syncthreads();
+            if (!lz_update(a, 0, cf, pr2, shp)) return;
+            b2 = lz_reduce_all(pr2, nb, shp, &bcast);
         }
     }
     // beta_k, v_{k+1}
     if (a.vnext) {
-        const double sc = b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0;
-        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += step)
-            a.vnext[i] = (T)(sc * widen(a.w[i]));
+        if (threadIdx.x == 0) {
+            float h, l;
+            split_f64(b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0, h, l);
+            scale = make_float2(h, l);
+        }
+        __syncthreads();
+        const float sh = scale.x, sl = scale.y;
+        const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+        for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += 2 * stride) {
+            const uint64_t i2 = i + stride;
+            const float2 rv = a.r[i];
+            const float2 rv2 = i2 < a.n ? a.r[i2] : make_float2(0.f, 0.f);
+            float vh, vl;
+            ff_mul(rv.x, rv.y, sh, sl, vh, vl);
+            st_basis(a.vnext + i, a.xnext + i, vh, vl);
+            if (i2 < a.n) {
+                ff_mul(rv2.x, rv2.y, sh, sl, vh, vl);
+                st_basis(a.vnext + i2, a.xnext + i2, vh, vl);
+            }
+        }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         a.alpha[a.k] = al;
@@ -356,30 +713,44 @@ __global__ void __launch_bounds__(kRedThreads) k_lz_step(LzStep<T> a) {
     }
 }
 
-// dst = src / sqrt(*nrm2) (the norm squared read from device memory); a zero norm (an exact
-// invariant subspace) gives a zero vector.
+// v_0 = v0 / sqrt(*nrm2) into the basis (and, for FP64 vectors, into the product input x0).
 template <typename T>
-__global__ void k_normalise(T* __restrict__ dst, const T* __restrict__ src, const double* __restrict__ nrm2,
-                            uint64_t n) {
+__global__ void k_lz_start(typename Basis<T>::S* V0, double* x0, const T* __restrict__ v0,
+                           const double* __restrict__ nrm2, uint64_t n) {
     const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        dst[i] = (T)(s * (double)src[i]);
-}
-
-// psi[i] = sum_{j<k} c[j] V_j[i] (FP64 arithmetic, stored in T); c staged in shared memory.
-template <typename T>
-__global__ void k_combination(T* __restrict__ psi, const T* __restrict__ V, size_t ldv, int k,
-                              const double* __restrict__ c, uint64_t n) {
-    extern __shared__ double cs[];
-    for (int q = threadIdx.x; q < k; q += blockDim.x) cs[q] = c[q];
-    __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int j = 0; j < k; ++j) acc += cs[j] * (double)__ldg(V + (size_t)j * ldv + i);
-        psi[i] = (T)acc;
+        float h, l;
+        split_f64(s * widen(v0[i]), h, l);
+        st_basis(V0 + i, x0 + i, h, l);
     }
 }
 
+// psi[i] = sum_{j<m} c[j] v_j[i] in double-single arithmetic (c split in shared memory).
+template <typename T>
+__global__ void k_combination(T* __restrict__ psi, const typename Basis<T>::S* V, size_t ldv, int m,
+                              const double* __restrict__ c, uint64_t n) {
+    extern __shared__ float2 cs[];
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        float h, l;
+        split_f64(c[q], h, l);
+        cs[q] = make_float2(h, l);
+    }
+    __syncthreads();
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        float fs = 0.f, fc = 0.f, s = 0.f, cc = 0.f;
+        for (int j = 0; j < m; ++j) {
+            float vh, vl;
+            ld_basis(V + (size_t)j * ldv + i, vh, vl);
+            ff_mac(s, cc, vh, vl, cs[j].x, cs[j].y);
+            if ((j + 1) % kFlush == 0) {
+                ff_fold(fs, fc, s, cc);
+                s = cc = 0.f;
+            }
+        }
+        ff_fold(fs, fc, s, cc);
+        st_value(psi + i, fs, fc);
+    }
+}
 // Number of eigenvalues of the symmetric tridiagonal T (diagonal a, off-diagonal b) below x.
 static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
     int cnt = 0;
@@ -506,6 +877,7 @@ struct Work {
 template <typename T>
 static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int steps, int reorth, double* E0,
                        double* alpha_out, double* beta_out, int* steps_done, T* psi, cudaStream_t st) {
+    using S = typename Basis<T>::S;
     const uint64_t D = s->D;
     const size_t ldv = (D + 31) & ~(size_t)31;
     const int sms = sm_count_cached();
@@ -513,22 +885,27 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return set_error(DQ_ECUDA, "Lanczos: the device does not support cooperative launches");
-    const size_t hsm = (size_t)(steps + 1) * sizeof(double);
+    const size_t smem_max = (size_t)(steps + 1) * (sizeof(double) + sizeof(float2));
     auto kern = k_lz_step<T>;
-    if (hsm > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hsm) != cudaSuccess)
+    if (smem_max > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) != cudaSuccess)
         return set_error(DQ_ECUDA, "Lanczos: shared memory for %d coefficients", steps + 1);
-    int per_sm = occupancy_cached(reinterpret_cast<const void*>(kern), kRedThreads, hsm);
-    if (per_sm > 4) per_sm = 4;
+    int per_sm = occupancy_cached(reinterpret_cast<const void*>(kern), kLzThreads, smem_max);
+    if (per_sm > 2) per_sm = 2;
+    if (per_sm < 1) return set_error(DQ_ECUDA, "Lanczos: the step kernel does not fit on an SM");
     const int nb = per_sm * sms;  // blocks of the cooperative step kernel (all resident)
     const int nbd = 2 * sms;      // blocks of the start-vector reduction
     int rc = DQ_OK;
     Work ws;
-    T* V = (T*)ws.get((size_t)(steps + 1) * ldv * sizeof(T), rc);
+    S* V = (S*)ws.get((size_t)(steps + 1) * ldv * sizeof(S), rc);
     if (!V) return rc;
     T* w = (T*)ws.get(ldv * sizeof(T), rc);
     if (!w) return rc;
-    const size_t npart = (size_t)nb * (steps + 6) > (size_t)nbd ? (size_t)nb * (steps + 6) : (size_t)nbd;
+    float2* r = (float2*)ws.get(ldv * sizeof(float2), rc);
+    if (!r) return rc;
+    double* x = nullptr;  // FP64 vectors: v_k in FP64, the product's input
+    if (sizeof(T) == 8 && !(x = (double*)ws.get(ldv * sizeof(double), rc))) return rc;
+    const size_t npart = (size_t)nb * (steps + 4) > (size_t)nbd ? (size_t)nb * (steps + 4) : (size_t)nbd;
     double* part = (double*)ws.get(npart * sizeof(double), rc);
     if (!part) return rc;
     // device doubles: h[0 .. steps], alpha[0 .. steps), beta2[0 .. steps), ||v0||^2
@@ -571,12 +948,13 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos start vector: %s", cudaGetErrorString(e));
     if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) return set_error(DQ_EINVAL, "v0 has zero or non-finite norm");
-    k_normalise<T><<<8 * sms, kRedThreads, 0, st>>>(V, v0, v0n, D);
+    k_lz_start<T><<<8 * sms, kRedThreads, 0, st>>>(V, x, v0, v0n, D);
 
     LzStep<T> arg;
     arg.ldv = ldv;
     arg.V = V;
     arg.w = w;
+    arg.r = r;
     arg.n = D;
     arg.reorth = reorth;
     arg.part = part;
@@ -603,7 +981,8 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
         m = q + 1;
         tnorm = std::fmax(tnorm, std::fmax(std::fabs(al), std::fmax(be, bprev)));
         bprev = be;
-        if (be < 1e-14 * tnorm) stop = true;
+        // an invariant subspace: the residual is at the level of the 48-bit arithmetic
+        if (be < 1e-12 * tnorm) stop = true;
         return DQ_OK;
     };
     int queued = 0;
@@ -612,13 +991,15 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
             if ((rc = consume(k - 2))) return rc;
             if (stop) break;
         }
-        T* vk = V + (size_t)k * ldv;
-        int le = launch_matvec(s, t, vk, w, dtype, 1, st);
+        const T* xk = sizeof(T) == 8 ? (const T*)x : (const T*)(V + (size_t)k * ldv);
+        int le = launch_matvec(s, t, xk, w, dtype, 1, st);
         if (le) return set_error(DQ_ECUDA, "matvec launch: %s", cudaGetErrorString((cudaError_t)le));
         arg.k = k;
         arg.vnext = k + 1 < steps ? V + (size_t)(k + 1) * ldv : nullptr;
+        arg.xnext = x;
         void* args[] = {&arg};
-        e = cudaLaunchCooperativeKernel((const void*)kern, dim3(nb), dim3(kRedThreads), args, (size_t)(k + 1) * 8, st);
+        const size_t smem = (size_t)(k + 1) * (sizeof(double) + sizeof(float2));
+        e = cudaLaunchCooperativeKernel((const void*)kern, dim3(nb), dim3(kLzThreads), args, smem, st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos step launch: %s", cudaGetErrorString(e));
         cudaEventRecord(ws.events[k % 3], st);
         if ((rc = cuda_fail("step"))) return rc;
@@ -641,7 +1022,7 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
         std::vector<double> y = m == 1 ? std::vector<double>{1.0} : tridiag_eigvec(a, off, e0);
         e = cudaMemcpyAsync(hv, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos Ritz vector: %s", cudaGetErrorString(e));
-        k_combination<T><<<8 * sms, kRedThreads, (size_t)m * sizeof(double), st>>>(psi, V, ldv, m, hv, D);
+        k_combination<T><<<8 * sms, kRedThreads, (size_t)m * sizeof(float2), st>>>(psi, V, ldv, m, hv, D);
         if ((rc = cuda_fail("Ritz vector"))) return rc;
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos: %s", cudaGetErrorString(e));
