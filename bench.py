@@ -254,7 +254,8 @@ def oracle_rows_rate(w, partition, x, seconds: float, steps: int | None = None, 
 
 def lanczos_check(b, torch):
     """Workload 1 (periodic Heisenberg chain L=20, N=10): 100 Lanczos steps through the library
-    with FP64 and FP32 vectors from the seeded start vector, against the oracle's E0 stored in
+    with FP64 and FP32 vectors from the seeded start vector, with FP64 passes over the basis and
+    with their double-single form, against the oracle's E0 stored in
     tests/golden/lanczos_workload1.txt. Wall-clock time of the synchronous call."""
     from paper_2407_14591_gb300 import workloads as wl
 
@@ -270,12 +271,13 @@ def lanczos_check(b, torch):
     w, x = wl.workload(1, D=s.dim)
     t = b.make_terms(s, w.terms)
     out = {"workload": w.name, "D": s.dim, "steps": steps, "E0_oracle": e_ref, "reorth": True}
-    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+    for dt, ds, name in ((torch.float64, False, "f64"), (torch.float32, False, "f32"),
+                         (torch.float64, True, "f64_double_single"), (torch.float32, True, "f32_double_single")):
         v0 = torch.from_numpy(x).to("cuda", dt)
-        b.lanczos(s, t, v0, steps)
+        b.lanczos(s, t, v0, steps, double_single=ds)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = b.lanczos(s, t, v0, steps)
+        r = b.lanczos(s, t, v0, steps, double_single=ds)
         el = time.perf_counter() - t0
         # the same number of products alone (CUDA events), for the cost of the rest of the step
         y = torch.empty_like(v0)
@@ -520,8 +522,9 @@ def run_lanczos(args, world, rank, local, dist, torch):
     """The Lanczos form of workload 2 (J1-J2 6x5, N = 15, D = 155,117,520) or, with
     --lanczos-workload bose, workload 3 (Bose-Hubbard Q = 4, L = 14, N = 14, D = 6,472,168), at
     full size: the same seeded start vector with FP64 vectors and with FP32 vectors (FP64
-    recurrence, dot products and updates in both), full re-orthogonalisation (classical
-    Gram-Schmidt twice per step). One JSON line: E0 of both, their relative difference, the
+    recurrence, dot products and updates in both; then both again with the double-single passes
+    over the basis), full re-orthogonalisation (classical Gram-Schmidt, a second pass when the
+    DGKS criterion asks for it). One JSON line: E0 of each, the FP32/FP64 relative difference, the
     residual ||H psi - E0 psi|| / |E0| of each Ritz vector (FP64), time per Lanczos step, and the
     product's share of it."""
     from paper_2407_14591_gb300 import binding as b
@@ -531,12 +534,13 @@ def run_lanczos(args, world, rank, local, dist, torch):
     w, s, x_np = build_workload(number, args.n_sub if number == 2 else None, args.N if number == 2 else None)
     t = b.make_terms(s, w.terms)
     out = {}
-    for dt, name in ((torch.float64, "f64"), (torch.float32, "f32")):
+    for dt, ds, name in ((torch.float64, False, "f64"), (torch.float32, False, "f32"),
+                         (torch.float64, True, "f64_double_single"), (torch.float32, True, "f32_double_single")):
         v0 = torch.from_numpy(x_np).to("cuda", dt)
-        b.lanczos(s, t, v0, 3, reorth=True)  # warm-up (scratch, tables)
+        b.lanczos(s, t, v0, 3, reorth=True, double_single=ds)  # warm-up (scratch, tables)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        r = b.lanczos(s, t, v0, steps, reorth=True, want_vector=True)
+        r = b.lanczos(s, t, v0, steps, reorth=True, want_vector=True, double_single=ds)
         el = time.perf_counter() - t0
         psi = r.pop("psi")
         hpsi = b.matvec(s, t, psi)
@@ -560,7 +564,7 @@ def run_lanczos(args, world, rank, local, dist, torch):
         print(json.dumps({"metric": "Lanczos E0, FP32 vectors vs FP64 vectors", "value": rel, "unit": "relative",
                           "higher_is_better": False, "n_gpus": world, "steps": steps, "data": "synthetic",
                           "config": {"workload": w.name, "D": s.dim, "n_sub": s.n_sub, "reorth": True},
-                          "f64": out["f64"], "f32": out["f32"]}), flush=True)
+                          **out}), flush=True)
 
 
 def main():

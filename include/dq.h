@@ -57,6 +57,10 @@ extern "C" {
 #define DQ_F64 0 /* vectors stored as double                                         */
 #define DQ_F32 1 /* vectors stored as float; accumulation is exact (fixed point)      */
 
+/* Flag OR'ed into dq_lanczos' reorth argument: double-single arithmetic for the passes over the
+ * Lanczos basis (see dq_lanczos). */
+#define DQ_LZ_DOUBLE_SINGLE 16
+
 /* ---- operator term kinds (all Hermitian, real) -------------------------------------------- */
 /* Spin-1/2 (Q = 2 only; a particle is an up spin, Sz = sigma - 1/2; App. D's Hamiltonian):  */
 #define DQ_XY 0  /* coef * 1/2 (S+_i S-_j + S-_i S+_j)                                        */
@@ -294,19 +298,22 @@ void dq_batch_free(dq_batch* b);
  * `dtype`, normalised inside the call, not modified), run up to `steps` steps of
  *   w = H v_k; alpha_k = <v_k, w>; w -= alpha_k v_k + beta_{k-1} v_{k-1};
  *   reorth == 1: full re-orthogonalisation by classical Gram-Schmidt against v_0 .. v_k,
- *                w -= V (V^T w), repeated once more when ||w|| after that pass is below
- *                1/sqrt(2) of sqrt(||w||^2 - h_k^2 - h_{k-1}^2) before it, what the three-term
- *                step alone would leave (the Daniel-Gragg-Kaufman-Stewart criterion);
+ *                w -= V (V^T w), repeated once more when that pass shrank ||w|| below 1/sqrt(2)
+ *                of its value before the pass (the Daniel-Gragg-Kaufman-Stewart criterion);
  *   reorth == 2: the same with the second pass always;
  *   reorth == 0: neither (the plain three-term recurrence);
  *   beta_k = ||w||; v_{k+1} = w / beta_k.
- * With reorth != 0 one pass computes h_j = <v_j, w> for every j <= k (alpha_k = h_k) and the
- * update w -= sum_j h_j v_j does the three-term step and the re-orthogonalisation at once.
- * Dot products, norms and vector updates use double-single arithmetic (pairs of floats with
- * error-free products and sums, about 48 significant bits; partial sums across threads in
- * FP64) whatever `dtype` is. The basis is stored as float pairs for DQ_F64 and as floats for
- * DQ_F32; the product reads v_k in `dtype`. E0 is the smallest eigenvalue of the tridiagonal
- * matrix T, found on the host by bisection on its Sturm sequence. The call stops early, without error,
+ * With reorth != 0 the three-term step is done on the fly inside the first Gram-Schmidt pass,
+ * whose coefficient for v_k is added to alpha_k. Dot products, norms, the recurrence and the
+ * vector updates are computed in FP64 whatever `dtype` is; the basis is stored in `dtype`.
+ * reorth | DQ_LZ_DOUBLE_SINGLE selects double-single arithmetic for every pass over the basis
+ * instead (pairs of floats with error-free products and sums, about 48 significant bits; block
+ * partials combined in FP64; the basis of DQ_F64 vectors stored as float pairs): several times
+ * faster on a GPU whose FP64 rate is a small fraction of its FP32 rate, at an accuracy close to
+ * FP64 (the recurrence coefficients and the tridiagonal solve stay FP64); pair elements below
+ * 2^-74 in magnitude keep 24 significant bits and below 2^-126 become zero, so the form suits
+ * operators whose coefficients are well above that scale. E0 is the smallest
+ * eigenvalue of the tridiagonal matrix T, found on the host by bisection on its Sturm sequence. The call stops early, without error,
  * when beta_k < 1e-12 * ||T||; *steps_done then holds the number of steps taken m. alpha and
  * beta (host, room for `steps` doubles each, may be NULL) receive the recurrence coefficients.
  * psi (device, D elements of `dtype`, may be NULL) receives the Ritz vector of E0,
@@ -317,7 +324,8 @@ void dq_batch_free(dq_batch* b);
  * call, and the product's own scratch is kept with the terms (see dq_matvec). The steps run on `stream` without waiting for the host: the call reads each
  * step's coefficients two steps later, so after a breakdown up to two more steps may have run;
  * their results are dropped. Synchronous: returns when E0 (and psi) are known. Errors: DQ_EINVAL
- * (NULL or out-of-range arguments, steps outside [1, 4096], reorth outside [0, 2], a zero or
+ * (NULL or out-of-range arguments, steps outside [1, 4096], reorth outside [0, 2] (apart from
+ * the flag), a zero or
  * non-finite v0), DQ_ENOMEM, DQ_ECUDA (also for a non-finite coefficient). */
 int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0, int steps, int dtype, int reorth,
                double* E0, double* alpha, double* beta, int* steps_done, void* psi, void* stream);

@@ -22,6 +22,7 @@ LIB_PATH = os.path.join(_HERE, "libdq_checked.so" if os.environ.get("DQ_CHECKED"
 
 DQ_OK, DQ_EINVAL, DQ_ERANGE, DQ_EINDEX, DQ_ESTATE, DQ_ENOMEM, DQ_ECUDA, DQ_EDEVICE = 0, -1, -2, -3, -4, -5, -6, -7
 DQ_F64, DQ_F32 = 0, 1
+DQ_LZ_DOUBLE_SINGLE = 16
 KINDS = {"XY": 0, "ZZ": 1, "Z": 2, "HOP": 3, "NN": 4, "N": 5, "U": 6}
 
 EXPORTED = (
@@ -419,11 +420,13 @@ def make_batch(sectors, terms, nrhs: int, dtype) -> Batch:
     return Batch(sectors, terms, nrhs, dtype)
 
 
-def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth=True, want_vector: bool = False) -> dict:
+def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth=True, want_vector: bool = False,
+            double_single: bool = False) -> dict:
     """Ground-state energy by Lanczos (synchronous). ``reorth``: False/0 none, True/1 full
-    re-orthogonalisation (second Gram-Schmidt pass when needed), 2 (second pass always). Returns
-    E0, alpha, beta, steps_done and, with ``want_vector``, the Ritz vector of E0 as ``psi`` (a CUDA
-    tensor like v0)."""
+    re-orthogonalisation (second Gram-Schmidt pass when needed), 2 (second pass always).
+    ``double_single``: the passes over the basis in double-single arithmetic instead of FP64.
+    Returns E0, alpha, beta, steps_done and, with ``want_vector``, the Ritz vector of E0 as
+    ``psi`` (a CUDA tensor like v0)."""
     import torch
 
     _check_vec(sector, v0, "v0")
@@ -435,7 +438,8 @@ def lanczos(sector: Sector, terms: Terms, v0, steps: int, reorth=True, want_vect
     done = ctypes.c_int()
     psi = torch.empty_like(v0) if want_vector else None
     _check(_lib.dq_lanczos(sector.handle, terms.handle, ctypes.c_void_p(v0.data_ptr()), steps, _dtype_code(v0),
-                           int(reorth), ctypes.byref(E0), alpha, beta, ctypes.byref(done),
+                           int(reorth) | (DQ_LZ_DOUBLE_SINGLE if double_single else 0), ctypes.byref(E0), alpha,
+                           beta, ctypes.byref(done),
                            ctypes.c_void_p(psi.data_ptr() if psi is not None else 0), _stream_handle()))
     m = done.value
     out = {"E0": E0.value, "alpha": np.array(alpha[:m]), "beta": np.array(beta[:m]), "steps_done": m}

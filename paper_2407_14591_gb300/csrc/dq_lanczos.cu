@@ -134,16 +134,23 @@ __global__ void __launch_bounds__(kRedThreads) k_gs_dots(const T* __restrict__ V
         }
 }
 
-// Exact widening of a float to double with integer operations (the hardware conversion runs on
-// the FP64 pipe); subnormals, Inf and NaN take the hardware path.
+// Exact widening of a float to double with integer operations only (the hardware conversion runs
+// on the FP64 pipe, and a branch to it would be compiled as a select that always executes it).
 __device__ __forceinline__ double widen(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
-                                    ((unsigned long long)(e + 896u) << 52) |
-                                    ((unsigned long long)(u & 0x7fffffu) << 29);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long bits;
+    if (e == 0xffu) {  // Inf, NaN
+        bits = sign | (0x7ffull << 52) | ((unsigned long long)m << 29);
+    } else if (e != 0u) {
+        bits = sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+    } else if (m == 0u) {
+        bits = sign;
+    } else {  // subnormal m * 2^-149, leading bit of m at position p: exponent p - 149
+        const int p = 31 - __clz(m);
+        bits = sign | ((unsigned long long)(p + 874) << 52) | (((unsigned long long)m << (52 - p)) & 0xfffffffffffffull);
+    }
     return __longlong_as_double((long long)bits);
 }
 __device__ __forceinline__ double widen(double d) { return d; }
@@ -258,95 +265,151 @@ __device__ __forceinline__ void ff_mul(float rh, float rl, float sh, float sl, f
 }
 
 // x = hi + lo with hi = x cut to 24 significant bits and lo the remainder rounded to FP32 (48
-// significant bits together), by integer operations when both are normal floats
-// (2^-74 <= |x| < 2^128); other x (zero, tiny, huge, Inf, NaN) take the hardware conversions.
+// significant bits together), by integer operations only. Magnitudes below 2^-126 become zero,
+// and below 2^-74 lo is dropped (it would not be a normal float); Inf and NaN give hi = x, lo = 0;
+// finite |x| >= 2^128 gives an infinite hi.
 __device__ __forceinline__ void split_f64(double x, float& hi, float& lo) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
     const unsigned e = (unsigned)(b >> 52) & 0x7ffu;
-    if (e >= 949u && e <= 1150u) {
-        const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if (e >= 897u && e <= 1150u) {
         hi = __uint_as_float(sign | ((e - 896u) << 23) | ((unsigned)(b >> 29) & 0x7fffffu));
-        const float scale = __uint_as_float(sign | ((e - 948u) << 23));  // +-2^(e - 1075)
-        lo = __fmul_rn(__uint2float_rn((unsigned)b & 0x1fffffffu), scale);
+        const float scale = __uint_as_float(sign | ((e >= 949u ? e - 948u : 0u) << 23));  // +-2^(e - 1075)
+        lo = e >= 949u ? __fmul_rn(__uint2float_rn((unsigned)b & 0x1fffffffu), scale) : 0.f;
+    } else if (e < 897u) {
+        hi = __uint_as_float(sign);
+        lo = 0.f;
     } else {
-        hi = __double2float_rn(x);
-        lo = __double2float_rn(x - (double)hi);
+        const bool nan = e == 0x7ffu && (b & 0xfffffffffffffull) != 0ull;
+        hi = __uint_as_float(sign | (nan ? 0x7fc00000u : 0x7f800000u));
+        lo = 0.f;
     }
 }
 
-// The basis: FP64 vectors keep each element as a float pair (hi, lo), FP32 vectors as a float.
+// ---- the arithmetic of the passes over the basis ---------------------------------------------
+// A policy fixes how an element is held in registers (E), how sums run (Sum), and the basis
+// element type S for vectors of type T.
+//   LzF64: FP64 elements and sums (fused multiply-adds on the FP64 pipe); the basis in T.
+//   LzDS: double-single elements and sums (above); the basis of FP64 vectors as float pairs,
+//         of FP32 vectors as floats.
+
 template <typename T>
-struct Basis;
+struct LzF64 {
+    using S = T;
+    using E = double;
+    struct Sum {
+        double s;
+    };
+    static constexpr bool kXBuffer = false;  // the product reads v_k from the basis itself
+    __device__ static E ld_basis(const T* p) { return widen(__ldg(p)); }
+    __device__ static E ld_w(const T* p) { return widen(__ldg(p)); }
+    __device__ static Sum zero() { return {0.0}; }
+    __device__ static void mac(Sum& a, E x, E y) { a.s = fma(x, y, a.s); }
+    __device__ static void sq(Sum& a, E x) { a.s = fma(x, x, a.s); }
+    __device__ static void fold(Sum& a, Sum b) { a.s += b.s; }
+    __device__ static Sum shfl_down(Sum a, int o) { return {__shfl_down_sync(0xffffffffu, a.s, o)}; }
+    __device__ static double value(Sum a) { return a.s; }
+    __device__ static Sum from_double(double x) { return {x}; }
+    __device__ static E coef(double c) { return c; }
+    __device__ static E sub(E r, Sum a) { return r - a.s; }
+    __device__ static E mul(E r, E c) { return r * c; }
+    __device__ static void st_basis(T* p, double*, E v) { *p = (T)v; }
+    __device__ static void st_out(T* p, Sum a) { *p = (T)a.s; }
+};
+
+template <typename T>
+struct LzDSBasis;
 template <>
-struct Basis<double> {
+struct LzDSBasis<double> {
     using S = float2;
 };
 template <>
-struct Basis<float> {
+struct LzDSBasis<float> {
     using S = float;
 };
-__device__ __forceinline__ void ld_basis(const float2* p, float& h, float& l) {
-    const float2 v = __ldg(p);
-    h = v.x;
-    l = v.y;
-}
-__device__ __forceinline__ void ld_basis(const float* p, float& h, float& l) {
-    h = __ldg(p);
-    l = 0.f;
-}
-// Store the renormalised pair (h, l) as a basis element; FP64 vectors also store its value in
-// FP64 (the next product's input), FP32 vectors store h + l rounded (itself that input).
-__device__ __forceinline__ void st_basis(float2* p, double* x, float h, float l) {
-    *p = make_float2(h, l);
-    *x = widen(h) + widen(l);
-}
-__device__ __forceinline__ void st_basis(float* p, double*, float h, float l) { *p = __fadd_rn(h, l); }
 
-// The product's output as a pair.
-__device__ __forceinline__ void ld_pair(const double* p, float& h, float& l) { split_f64(__ldg(p), h, l); }
-__device__ __forceinline__ void ld_pair(const float* p, float& h, float& l) {
-    h = __ldg(p);
-    l = 0.f;
-}
-__device__ __forceinline__ void st_value(double* p, float h, float l) { *p = widen(h) + widen(l); }
-__device__ __forceinline__ void st_value(float* p, float h, float l) { *p = __fadd_rn(h, l); }
-
-// Sum of the pairs (S, C) of the block, in FP64 in thread 0 (shp: 32 pairs).
-__device__ __forceinline__ double block_pair_sum(float S, float C, float2* shp) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const float so = __shfl_down_sync(0xffffffffu, S, o), co = __shfl_down_sync(0xffffffffu, C, o);
-        ff_fold(S, C, so, co);
+template <typename T>
+struct LzDS {
+    using S = typename LzDSBasis<T>::S;
+    using E = float2;
+    struct Sum {
+        float s, c;
+    };
+    static constexpr bool kXBuffer = sizeof(T) == 8;  // FP64 vectors: the product reads an FP64 copy
+    __device__ static E ld_basis(const float2* p) { return __ldg(p); }
+    __device__ static E ld_basis(const float* p) { return make_float2(__ldg(p), 0.f); }
+    __device__ static E ld_w(const double* p) {
+        float h, l;
+        split_f64(__ldg(p), h, l);
+        return make_float2(h, l);
     }
+    __device__ static E ld_w(const float* p) { return make_float2(__ldg(p), 0.f); }
+    __device__ static Sum zero() { return {0.f, 0.f}; }
+    __device__ static void mac(Sum& a, E x, E y) { ff_mac(a.s, a.c, x.x, x.y, y.x, y.y); }
+    __device__ static void sq(Sum& a, E x) { ff_sq(a.s, a.c, x.x, x.y); }
+    __device__ static void fold(Sum& a, Sum b) { ff_fold(a.s, a.c, b.s, b.c); }
+    __device__ static Sum shfl_down(Sum a, int o) {
+        return {__shfl_down_sync(0xffffffffu, a.s, o), __shfl_down_sync(0xffffffffu, a.c, o)};
+    }
+    __device__ static double value(Sum a) { return widen(a.s) + widen(a.c); }
+    __device__ static Sum from_double(double x) {
+        Sum a;
+        split_f64(x, a.s, a.c);
+        return a;
+    }
+    __device__ static E coef(double c) {
+        float h, l;
+        split_f64(c, h, l);
+        return make_float2(h, l);
+    }
+    __device__ static E sub(E r, Sum a) {
+        float h, l;
+        ff_sub(r.x, r.y, a.s, a.c, h, l);
+        return make_float2(h, l);
+    }
+    __device__ static E mul(E r, E c) {
+        float h, l;
+        ff_mul(r.x, r.y, c.x, c.y, h, l);
+        return make_float2(h, l);
+    }
+    __device__ static void st_basis(float2* p, double* x, E v) {
+        *p = v;
+        *x = widen(v.x) + widen(v.y);
+    }
+    __device__ static void st_basis(float* p, double*, E v) { *p = __fadd_rn(v.x, v.y); }
+    __device__ static void st_out(double* p, Sum a) { *p = widen(a.s) + widen(a.c); }
+    __device__ static void st_out(float* p, Sum a) { *p = __fadd_rn(a.s, a.c); }
+};
+
+template <class P>
+__device__ __forceinline__ typename P::Sum warp_sum(typename P::Sum a) {
+    for (int o = 16; o > 0; o >>= 1) P::fold(a, P::shfl_down(a, o));
+    return a;
+}
+
+// Sum over the block, in FP64 in thread 0 (sh: 32 sums).
+template <class P>
+__device__ __forceinline__ double block_total(typename P::Sum a, typename P::Sum* sh) {
+    a = warp_sum<P>(a);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) shp[wid] = make_float2(S, C);
+    if (lane == 0) sh[wid] = a;
     __syncthreads();
     double r = 0.0;
     if (wid == 0) {
-        float s = 0.f, c = 0.f;
-        if (lane < (int)(blockDim.x >> 5)) {
-            s = shp[lane].x;
-            c = shp[lane].y;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float so = __shfl_down_sync(0xffffffffu, s, o), co = __shfl_down_sync(0xffffffffu, c, o);
-            ff_fold(s, c, so, co);
-        }
-        r = widen(s) + widen(c);
+        typename P::Sum b = lane < (int)(blockDim.x >> 5) ? sh[lane] : P::zero();
+        r = P::value(warp_sum<P>(b));
     }
     __syncthreads();
     return r;
 }
 
-// Sum of the FP64 block partials part[0 .. nb) in a fixed order, in float pairs, returned to
-// every thread of the block; every block gets the same value.
-__device__ __forceinline__ double lz_reduce_all(const double* part, int nb, float2* shp, double* bc) {
-    float s = 0.f, c = 0.f;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-        float h, l;
-        split_f64(__ldcg(part + b), h, l);
-        ff_fold(s, c, h, l);
-    }
-    const double v = block_pair_sum(s, c, shp);
+// Sum of the FP64 block partials part[0 .. nb) in a fixed order, returned to every thread of the
+// block; every block gets the same value.
+template <class P>
+__device__ __forceinline__ double lz_reduce_all(const double* part, int nb, typename P::Sum* sh, double* bc) {
+    typename P::Sum a = P::zero();
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) P::fold(a, P::from_double(__ldcg(part + b)));
+    const double v = block_total<P>(a, sh);
     if (threadIdx.x == 0) *bc = v;
     __syncthreads();
     const double r = *bc;
@@ -354,16 +417,17 @@ __device__ __forceinline__ double lz_reduce_all(const double* part, int nb, floa
     return r;
 }
 
-template <typename T>
+template <typename T, class P>
 struct LzStep {
-    using S = typename Basis<T>::S;
+    using S = typename P::S;
+    using E = typename P::E;
     const S* V;       // basis v_0 .. v_k, stride ldv
     size_t ldv;
     int k;            // step index
     const T* w;       // H v_k (the product's output)
-    float2* r;        // the residual as float pairs
+    E* r;             // the residual
     S* vnext;         // v_{k+1} in the basis (NULL at the last step)
-    double* xnext;    // v_{k+1} in FP64 for the next product (FP64 vectors)
+    double* xnext;    // v_{k+1} in FP64 for the next product (double-single, FP64 vectors)
     uint64_t n;
     int reorth;       // 0, 1 (DGKS second pass), 2 (second pass always)
     double* part;     // per-block partial sums, gridDim.x * (k + 5) doubles
@@ -375,38 +439,33 @@ struct LzStep {
     int* fail;        // barrier timeout
 };
 
-
-// alpha pass: the block partial of <v_k, w> into pa[b]; w is also stored as float pairs in r.
+// alpha pass: the block partial of <v_k, w> into pa[b]; w is also stored as the residual r.
 // Two elements per iteration, so that each thread has four loads in flight.
-template <typename T>
-__device__ bool lz_alpha(const LzStep<T>& a, const typename Basis<T>::S* vk, double* pa, float2* shp) {
+template <typename T, class P>
+__device__ bool lz_alpha(const LzStep<T, P>& a, const typename P::S* vk, double* pa, typename P::Sum* sh) {
+    using Sum = typename P::Sum;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    float s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f;
+    Sum s1 = P::zero(), s2 = P::zero();
     int cnt = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += 2 * stride) {
         const uint64_t i2 = i + stride;
         const bool two = i2 < a.n;
-        float wh, wl, vh, vl, wh2 = 0.f, wl2 = 0.f, vh2 = 0.f, vl2 = 0.f;
-        ld_pair(a.w + i, wh, wl);
-        ld_basis(vk + i, vh, vl);
+        const typename P::E w1 = P::ld_w(a.w + i), v1 = P::ld_basis(vk + i);
+        const typename P::E w2 = two ? P::ld_w(a.w + i2) : w1, v2 = two ? P::ld_basis(vk + i2) : v1;
+        a.r[i] = w1;
+        P::mac(s1, v1, w1);
         if (two) {
-            ld_pair(a.w + i2, wh2, wl2);
-            ld_basis(vk + i2, vh2, vl2);
-        }
-        a.r[i] = make_float2(wh, wl);
-        ff_mac(s1, c1, vh, vl, wh, wl);
-        if (two) {
-            a.r[i2] = make_float2(wh2, wl2);
-            ff_mac(s1, c1, vh2, vl2, wh2, wl2);
+            a.r[i2] = w2;
+            P::mac(s1, v2, w2);
         }
         if (++cnt == kFlush / 2) {
             cnt = 0;
-            ff_fold(s2, c2, s1, c1);
-            s1 = c1 = 0.f;
+            P::fold(s2, s1);
+            s1 = P::zero();
         }
     }
-    ff_fold(s2, c2, s1, c1);
-    const double v = block_pair_sum(s2, c2, shp);
+    P::fold(s2, s1);
+    const double v = block_total<P>(s2, sh);
     if (threadIdx.x == 0) pa[blockIdx.x] = v;
     return grid_sync(a.bar, a.fail);
 }
@@ -421,17 +480,18 @@ __device__ __forceinline__ void lz_slab(uint64_t n, uint64_t& lo, uint64_t& hi) 
 
 // Projection pass: block partials pd[b * (k + 1) + j] of h_j = <v_j, r> for j <= k. Block b owns
 // a contiguous slab of elements; its warps share the basis vectors in tiles of kLzTile (warp w
-// takes tiles w, w + 8, ...), each lane summing its strided elements of the slab in float pairs
-// (folded every kFlush elements into a second pair kept in shared memory, fls, so that four
-// blocks fit on an SM without register spills), and a shuffle tree gives the warp's partial
-// for each vector of the tile. No block barrier inside the tiles, so they proceed side by side;
-// with fewer tiles than warps, several warps share a tile (wp: their sums). first: before the tiles, the block replaces r (holding w) on its slab by the
-// three-term remainder r - alpha v_k - beta v_{k-1} (ab = alpha and beta as float pairs) and puts
-// ||r||^2 into pw[b].
-template <typename T>
-__device__ bool lz_project(const LzStep<T>& a, float4 ab, bool first, double* pd, double* pw, float2* shp,
-                           float2* wp, float2* fls) {
-    using S = typename Basis<T>::S;
+// takes tiles w, w + 16, ...), each lane summing its strided elements of the slab (folded every
+// kFlush elements into a second sum kept in shared memory, fls, so that registers stay few), and
+// a shuffle tree gives the warp's partial for each vector of the tile. No block barrier inside
+// the tiles, so they proceed side by side; with fewer tiles than warps, several warps share a
+// tile (wp: their sums). first: before the tiles, the block replaces r (holding w) on its slab by
+// the three-term remainder r - alpha v_k - beta v_{k-1} and puts ||r||^2 into pw[b].
+template <typename T, class P>
+__device__ bool lz_project(const LzStep<T, P>& a, typename P::E al, typename P::E be, bool first, double* pd,
+                           double* pw, typename P::Sum* sh, typename P::Sum* wp, typename P::Sum* fls) {
+    using S = typename P::S;
+    using E = typename P::E;
+    using Sum = typename P::Sum;
     const int nj = a.k + 1;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     uint64_t lo, hi;
@@ -439,117 +499,100 @@ __device__ bool lz_project(const LzStep<T>& a, float4 ab, bool first, double* pd
     if (first) {
         const S* vk = a.V + (size_t)a.k * a.ldv;
         const S* vp = a.k ? vk - a.ldv : nullptr;
-        float ns = 0.f, nc = 0.f, ns2 = 0.f, nc2 = 0.f;
+        Sum n1 = P::zero(), n2 = P::zero();
         int cnt = 0;
         for (uint64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-            const float2 rv = a.r[i];
-            float ts = 0.f, tc = 0.f, uh, ul, wh, wl;
-            ld_basis(vk + i, uh, ul);
-            ff_mac(ts, tc, uh, ul, ab.x, ab.y);
-            if (vp) {
-                ld_basis(vp + i, uh, ul);
-                ff_mac(ts, tc, uh, ul, ab.z, ab.w);
-            }
-            ff_sub(rv.x, rv.y, ts, tc, wh, wl);
-            a.r[i] = make_float2(wh, wl);
-            ff_sq(ns, nc, wh, wl);
+            Sum t = P::zero();
+            P::mac(t, P::ld_basis(vk + i), al);
+            if (vp) P::mac(t, P::ld_basis(vp + i), be);
+            const E w = P::sub(a.r[i], t);
+            a.r[i] = w;
+            P::sq(n1, w);
             if (++cnt == kFlush) {
                 cnt = 0;
-                ff_fold(ns2, nc2, ns, nc);
-                ns = nc = 0.f;
+                P::fold(n2, n1);
+                n1 = P::zero();
             }
         }
-        ff_fold(ns2, nc2, ns, nc);
-        const double v = block_pair_sum(ns2, nc2, shp);  // also orders the writes to r above
+        P::fold(n2, n1);
+        const double v = block_total<P>(n2, sh);  // also orders the writes to r above
         if (threadIdx.x == 0) pw[blockIdx.x] = v;
     }
-    // P warps per tile when there are fewer tiles than warps (each takes every P-th 32-element
+    // P warps per tile when there are fewer tiles than warps (each takes every Pw-th 32-element
     // chunk of the slab; their sums are combined through shared memory in part order)
     const int ntile = (nj + kLzTile - 1) / kLzTile;
-    const int P = ntile >= nw ? 1 : nw / ntile;
-    const int part = wid % P;
-    for (int t0 = (wid / P) * kLzTile; t0 < nj; t0 += (nw / P) * kLzTile) {
+    const int Pw = ntile >= nw ? 1 : nw / ntile;
+    const int part = wid % Pw;
+    for (int t0 = (wid / Pw) * kLzTile; t0 < nj; t0 += (nw / Pw) * kLzTile) {
         const int nt = nj - t0 < kLzTile ? nj - t0 : kLzTile;
         const S* Vb = a.V + (size_t)t0 * a.ldv;
-        float s1[kLzTile], c1[kLzTile];
-        float2* fl = fls + wid * kLzTile * 32 + lane;  // this lane's second-level pairs
+        Sum s1[kLzTile];
+        Sum* fl = fls + wid * kLzTile * 32 + lane;  // this lane's second-level sums
 #pragma unroll
         for (int q = 0; q < kLzTile; ++q) {
-            s1[q] = c1[q] = 0.f;
-            fl[q * 32] = make_float2(0.f, 0.f);
+            s1[q] = P::zero();
+            fl[q * 32] = P::zero();
         }
         int cnt = 0;
-        for (uint64_t i = lo + 32 * part + lane; i < hi; i += 32 * P) {
-            const float2 rv = a.r[i];
-            float vh[kLzTile], vl[kLzTile];
+        for (uint64_t i = lo + 32 * part + lane; i < hi; i += 32 * Pw) {
+            const E rv = a.r[i];
+            E v[kLzTile];
 #pragma unroll
             for (int q = 0; q < kLzTile; ++q) {
-                vh[q] = vl[q] = 0.f;
-                if (q < nt) ld_basis(Vb + (size_t)q * a.ldv + i, vh[q], vl[q]);
+                v[q] = E{};
+                if (q < nt) v[q] = P::ld_basis(Vb + (size_t)q * a.ldv + i);
             }
 #pragma unroll
-            for (int q = 0; q < kLzTile; ++q) ff_mac(s1[q], c1[q], vh[q], vl[q], rv.x, rv.y);
+            for (int q = 0; q < kLzTile; ++q) P::mac(s1[q], v[q], rv);
             if (++cnt == kFlush) {
                 cnt = 0;
 #pragma unroll
                 for (int q = 0; q < kLzTile; ++q) {
-                    float2 m = fl[q * 32];
-                    ff_fold(m.x, m.y, s1[q], c1[q]);
+                    Sum m = fl[q * 32];
+                    P::fold(m, s1[q]);
                     fl[q * 32] = m;
-                    s1[q] = c1[q] = 0.f;
+                    s1[q] = P::zero();
                 }
             }
         }
 #pragma unroll
         for (int q = 0; q < kLzTile; ++q) {
-            float2 m = fl[q * 32];
-            ff_fold(m.x, m.y, s1[q], c1[q]);
-            for (int o = 16; o > 0; o >>= 1) {
-                const float so = __shfl_down_sync(0xffffffffu, m.x, o);
-                const float co = __shfl_down_sync(0xffffffffu, m.y, o);
-                ff_fold(m.x, m.y, so, co);
-            }
+            Sum m = fl[q * 32];
+            P::fold(m, s1[q]);
+            m = warp_sum<P>(m);
             if (lane == 0 && q < nt) {
-                if (P == 1)
-                    pd[(size_t)blockIdx.x * nj + t0 + q] = widen(m.x) + widen(m.y);
+                if (Pw == 1)
+                    pd[(size_t)blockIdx.x * nj + t0 + q] = P::value(m);
                 else
                     wp[wid * kLzTile + q] = m;
             }
         }
     }
-    if (P > 1) {
+    if (Pw > 1) {
         __syncthreads();
         for (int j = threadIdx.x; j < nj; j += blockDim.x) {
-            const int w0 = (j / kLzTile) * P, q = j % kLzTile;
-            float sq = 0.f, cq = 0.f;
-            for (int p = 0; p < P; ++p) ff_fold(sq, cq, wp[(w0 + p) * kLzTile + q].x, wp[(w0 + p) * kLzTile + q].y);
-            pd[(size_t)blockIdx.x * nj + j] = widen(sq) + widen(cq);
+            const int w0 = (j / kLzTile) * Pw, q = j % kLzTile;
+            Sum m = P::zero();
+            for (int p = 0; p < Pw; ++p) P::fold(m, wp[(w0 + p) * kLzTile + q]);
+            pd[(size_t)blockIdx.x * nj + j] = P::value(m);
         }
     }
     return grid_sync(a.bar, a.fail);
 }
 
-// h_j for j <= k from the block partials: one warp per vector sums the blocks' partials in float
-// pairs in a fixed order (lane l takes blocks l, l + 32, ..., then a shuffle tree). With at most
-// as many vectors as a block has warps every block does this for all of them into hd (no grid
-// barrier); otherwise the warps of the grid share the vectors, write a.h, and after a barrier
-// each block copies a.h into hd. Either way every block holds the same values.
-template <typename T>
-__device__ bool lz_reduce(const LzStep<T>& a, const double* pd, double* hd) {
+// h_j for j <= k from the block partials: one warp per vector sums the blocks' partials in a
+// fixed order (lane l takes blocks l, l + 32, ..., then a shuffle tree). With at most as many
+// vectors as a block has warps every block does this for all of them into hd (no grid barrier);
+// otherwise the warps of the grid share the vectors, write a.h, and after a barrier each block
+// copies a.h into hd. Either way every block holds the same values.
+template <typename T, class P>
+__device__ bool lz_reduce(const LzStep<T, P>& a, const double* pd, double* hd) {
     const int nj = a.k + 1, nb = gridDim.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     auto column = [&](int j) {
-        float s = 0.f, c = 0.f;
-        for (int b = lane; b < nb; b += 32) {
-            float h, l;
-            split_f64(__ldcg(pd + (size_t)b * nj + j), h, l);
-            ff_fold(s, c, h, l);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float so = __shfl_down_sync(0xffffffffu, s, o), co = __shfl_down_sync(0xffffffffu, c, o);
-            ff_fold(s, c, so, co);
-        }
-        return widen(s) + widen(c);
+        typename P::Sum m = P::zero();
+        for (int b = lane; b < nb; b += 32) P::fold(m, P::from_double(__ldcg(pd + (size_t)b * nj + j)));
+        return P::value(warp_sum<P>(m));
     };
     if (nj <= nw) {
         if (wid < nj) {
@@ -569,139 +612,114 @@ __device__ bool lz_reduce(const LzStep<T>& a, const double* pd, double* hd) {
     return true;
 }
 
-// Update pass: r -= sum_{j in [u0, k]} c_j v_j over the thread's elements (c as float pairs in
-// cf), ten (float pairs) or sixteen (floats) basis loads in flight per round and two
-// independent pair sums over j, folded into one every 4 kFlush terms; then the block partial of
-// ||r||^2 into pr[b].
-template <typename T>
-__device__ bool lz_update(const LzStep<T>& a, int u0, const float2* cf, double* pr, float2* shp) {
-    constexpr int kG = sizeof(typename Basis<T>::S) == 8 ? 10 : 16;  // loads per round (registers)
+// Update pass: r -= sum_{j in [u0, k]} c_j v_j over the thread's elements (coefficients in cf),
+// kG basis loads in flight per round (padded rounds load zeros) and two independent sums over j,
+// folded into one every 4 kFlush terms; then the block partial of ||r||^2 into pr[b].
+template <typename T, class P>
+__device__ bool lz_update(const LzStep<T, P>& a, int u0, const typename P::E* cf, double* pr,
+                          typename P::Sum* sh) {
+    using E = typename P::E;
+    using Sum = typename P::Sum;
+    constexpr int kG = 10;  // loads per round (registers)
     const int kk = a.k + 1;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    float ns = 0.f, nc = 0.f, ns2 = 0.f, nc2 = 0.f;
+    Sum n1 = P::zero(), n2 = P::zero();
     int cnt = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += stride) {
-        float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, fs = 0.f, fc = 0.f;
+        Sum s0 = P::zero(), s1 = P::zero(), fs = P::zero();
         for (int j0 = u0; j0 < kk; j0 += 4 * kFlush) {
             const int je = kk - j0 < 4 * kFlush ? kk : j0 + 4 * kFlush;
-            for (int j = j0; j < je; j += kG) {  // kG loads in flight; past je they are zeros
-                float vh[kG], vl[kG];
+            for (int j = j0; j < je; j += kG) {
+                E v[kG];
 #pragma unroll
                 for (int q = 0; q < kG; ++q) {
-                    vh[q] = vl[q] = 0.f;
-                    if (j + q < je) ld_basis(a.V + (size_t)(j + q) * a.ldv + i, vh[q], vl[q]);
+                    v[q] = E{};
+                    if (j + q < je) v[q] = P::ld_basis(a.V + (size_t)(j + q) * a.ldv + i);
                 }
                 // a padded term multiplies a zero by the last (finite) coefficient
 #pragma unroll
                 for (int q = 0; q < kG; q += 2) {
-                    const float2 ca = cf[j + q < je ? j + q : je - 1], cb = cf[j + q + 1 < je ? j + q + 1 : je - 1];
-                    ff_mac(s0, c0, vh[q], vl[q], ca.x, ca.y);
-                    ff_mac(s1, c1, vh[q + 1], vl[q + 1], cb.x, cb.y);
+                    P::mac(s0, v[q], cf[j + q < je ? j + q : je - 1]);
+                    P::mac(s1, v[q + 1], cf[j + q + 1 < je ? j + q + 1 : je - 1]);
                 }
             }
-            ff_fold(fs, fc, s0, c0);
-            ff_fold(fs, fc, s1, c1);
-            s0 = c0 = s1 = c1 = 0.f;
+            P::fold(fs, s0);
+            P::fold(fs, s1);
+            s0 = s1 = P::zero();
         }
-        const float2 rv = a.r[i];
-        float rh, rl;
-        ff_sub(rv.x, rv.y, fs, fc, rh, rl);
-        a.r[i] = make_float2(rh, rl);
-        ff_sq(ns, nc, rh, rl);
+        const E rn = P::sub(a.r[i], fs);
+        a.r[i] = rn;
+        P::sq(n1, rn);
         if (++cnt == kFlush) {
             cnt = 0;
-            ff_fold(ns2, nc2, ns, nc);
-            ns = nc = 0.f;
+            P::fold(n2, n1);
+            n1 = P::zero();
         }
     }
-    ff_fold(ns2, nc2, ns, nc);
-    const double v = block_pair_sum(ns2, nc2, shp);
+    P::fold(n2, n1);
+    const double v = block_total<P>(n2, sh);
     if (threadIdx.x == 0) pr[blockIdx.x] = v;
     return grid_sync(a.bar, a.fail);
 }
 
 // One Lanczos step after the product (see the file comment). Cooperative launch; dynamic shared
-// memory: k + 1 doubles (the coefficients) and k + 1 float pairs (the coefficients split).
-template <typename T>
-__global__ void __launch_bounds__(kLzThreads, 2) k_lz_step(LzStep<T> a) {
+// memory: k + 1 doubles (the coefficients) and k + 1 elements E (the coefficients converted).
+template <typename T, class P>
+__global__ void __launch_bounds__(kLzThreads, 2) k_lz_step(LzStep<T, P> a) {
+    using E = typename P::E;
+    using Sum = typename P::Sum;
     extern __shared__ __align__(16) unsigned char lz_smem[];
     double* hd = reinterpret_cast<double*>(lz_smem);
-    float2* cf = reinterpret_cast<float2*>(hd + a.k + 1);
-    __shared__ float2 shp[32];
+    E* cf = reinterpret_cast<E*>(hd + a.k + 1);
+    __shared__ Sum sh[32];
     __shared__ double bcast;
-    __shared__ float2 scale;
-    __shared__ float2 wp[kLzThreads / 32 * kLzTile];        // the projection's per-warp sums
-    __shared__ float2 fls[kLzThreads / 32 * kLzTile * 32];  // its per-lane second-level pairs
+    __shared__ Sum wp[kLzThreads / 32 * kLzTile];        // the projection's per-warp sums
+    __shared__ Sum fls[kLzThreads / 32 * kLzTile * 32];  // its per-lane second-level sums
     const int nb = gridDim.x, kk = a.k + 1;
     double* pa = a.part;   // <v_k, w>
     double* pw = pa + nb;  // ||r||^2 after the three-term step
     double* pr1 = pw + nb; // after the first Gram-Schmidt pass (or the three-term update)
     double* pr2 = pr1 + nb;
     double* pd = pr2 + nb; // projection partials, nb * (k + 1)
-    if (!lz_alpha(a, a.V + (size_t)a.k * a.ldv, pa, shp)) return;
-    double al = lz_reduce_all(pa, nb, shp, &bcast);
+    if (!lz_alpha(a, a.V + (size_t)a.k * a.ldv, pa, sh)) return;
+    double al = lz_reduce_all<P>(pa, nb, sh, &bcast);
     const double be = a.k ? sqrt(__ldcg(a.beta2 + a.k - 1)) : 0.0;
     double b2;
     if (!a.reorth) {  // r -= alpha_k v_k + beta_{k-1} v_{k-1}
-        if (threadIdx.x < 2 && (threadIdx.x == 0 || a.k)) {
-            float h, l;
-            split_f64(threadIdx.x ? be : al, h, l);
-            cf[a.k - threadIdx.x] = make_float2(h, l);
-        }
+        if (threadIdx.x < 2 && (threadIdx.x == 0 || a.k)) cf[a.k - threadIdx.x] = P::coef(threadIdx.x ? be : al);
         __syncthreads();
-        if (!lz_update(a, a.k ? a.k - 1 : 0, cf, pr1, shp)) return;
-        b2 = lz_reduce_all(pr1, nb, shp, &bcast);
+        if (!lz_update(a, a.k ? a.k - 1 : 0, cf, pr1, sh)) return;
+        b2 = lz_reduce_all<P>(pr1, nb, sh, &bcast);
     } else {
-        float4 ab;
-        split_f64(al, ab.x, ab.y);
-        split_f64(be, ab.z, ab.w);
-        if (!lz_project(a, ab, true, pd, pw, shp, wp, fls)) return;
+        const E ale = P::coef(al), bee = P::coef(be);
+        if (!lz_project(a, ale, bee, true, pd, pw, sh, wp, fls)) return;
         if (!lz_reduce(a, pd, hd)) return;
         al += hd[a.k];
-        for (int j = threadIdx.x; j < kk; j += blockDim.x) {
-            float h, l;
-            split_f64(hd[j], h, l);
-            cf[j] = make_float2(h, l);
-        }
+        for (int j = threadIdx.x; j < kk; j += blockDim.x) cf[j] = P::coef(hd[j]);
         __syncthreads();
-        if (!lz_update(a, 0, cf, pr1, shp)) return;
-        b2 = lz_reduce_all(pr1, nb, shp, &bcast);
-        const double rho0 = lz_reduce_all(pw, nb, shp, &bcast);
+        if (!lz_update(a, 0, cf, pr1, sh)) return;
+        b2 = lz_reduce_all<P>(pr1, nb, sh, &bcast);
+        const double rho0 = lz_reduce_all<P>(pw, nb, sh, &bcast);
         if (a.reorth == 2 || b2 < 0.5 * rho0) {
-            if (!lz_project(a, ab, false, pd, nullptr, shp, wp, fls)) return;
+            if (!lz_project(a, ale, bee, false, pd, nullptr, sh, wp, fls)) return;
             if (!lz_reduce(a, pd, hd)) return;
             al += hd[a.k];
-            for (int j = threadIdx.x; j < kk; j += blockDim.x) {
-                float h, l;
-                split_f64(hd[j], h, l);
-                cf[j] = make_float2(h, l);
-            }
+            for (int j = threadIdx.x; j < kk; j += blockDim.x) cf[j] = P::coef(hd[j]);
             __syncthreads();
-            if (!lz_update(a, 0, cf, pr2, shp)) return;
-            b2 = lz_reduce_all(pr2, nb, shp, &bcast);
+            if (!lz_update(a, 0, cf, pr2, sh)) return;
+            b2 = lz_reduce_all<P>(pr2, nb, sh, &bcast);
         }
     }
     // beta_k, v_{k+1}
     if (a.vnext) {
-        if (threadIdx.x == 0) {
-            float h, l;
-            split_f64(b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0, h, l);
-            scale = make_float2(h, l);
-        }
-        __syncthreads();
-        const float sh = scale.x, sl = scale.y;
+        const E sc = P::coef(b2 > 0.0 ? 1.0 / sqrt(b2) : 0.0);
         const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
         for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.n; i += 2 * stride) {
             const uint64_t i2 = i + stride;
-            const float2 rv = a.r[i];
-            const float2 rv2 = i2 < a.n ? a.r[i2] : make_float2(0.f, 0.f);
-            float vh, vl;
-            ff_mul(rv.x, rv.y, sh, sl, vh, vl);
-            st_basis(a.vnext + i, a.xnext + i, vh, vl);
-            if (i2 < a.n) {
-                ff_mul(rv2.x, rv2.y, sh, sl, vh, vl);
-                st_basis(a.vnext + i2, a.xnext + i2, vh, vl);
-            }
+            const E r1 = a.r[i];
+            const E r2 = i2 < a.n ? a.r[i2] : r1;
+            P::st_basis(a.vnext + i, a.xnext + i, P::mul(r1, sc));
+            if (i2 < a.n) P::st_basis(a.vnext + i2, a.xnext + i2, P::mul(r2, sc));
         }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -713,44 +731,38 @@ __global__ void __launch_bounds__(kLzThreads, 2) k_lz_step(LzStep<T> a) {
     }
 }
 
-// v_0 = v0 / sqrt(*nrm2) into the basis (and, for FP64 vectors, into the product input x0).
-template <typename T>
-__global__ void k_lz_start(typename Basis<T>::S* V0, double* x0, const T* __restrict__ v0,
-                           const double* __restrict__ nrm2, uint64_t n) {
+// v_0 = v0 / sqrt(*nrm2) into the basis (and, with an FP64 copy, into the product input x0).
+template <typename T, class P>
+__global__ void k_lz_start(typename P::S* V0, double* x0, const T* __restrict__ v0, const double* __restrict__ nrm2,
+                           uint64_t n) {
     const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        P::st_basis(V0 + i, x0 + i, P::coef(s * widen(v0[i])));
+}
+
+// psi[i] = sum_{j<m} c[j] v_j[i] (c converted in shared memory).
+template <typename T, class P>
+__global__ void k_combination(T* __restrict__ psi, const typename P::S* V, size_t ldv, int m,
+                              const double* __restrict__ c, uint64_t n) {
+    using E = typename P::E;
+    extern __shared__ __align__(16) unsigned char cmb_smem[];
+    E* cs = reinterpret_cast<E*>(cmb_smem);
+    for (int q = threadIdx.x; q < m; q += blockDim.x) cs[q] = P::coef(c[q]);
+    __syncthreads();
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        float h, l;
-        split_f64(s * widen(v0[i]), h, l);
-        st_basis(V0 + i, x0 + i, h, l);
+        typename P::Sum s1 = P::zero(), s2 = P::zero();
+        for (int j = 0; j < m; ++j) {
+            P::mac(s1, P::ld_basis(V + (size_t)j * ldv + i), cs[j]);
+            if ((j + 1) % kFlush == 0) {
+                P::fold(s2, s1);
+                s1 = P::zero();
+            }
+        }
+        P::fold(s2, s1);
+        P::st_out(psi + i, s2);
     }
 }
 
-// psi[i] = sum_{j<m} c[j] v_j[i] in double-single arithmetic (c split in shared memory).
-template <typename T>
-__global__ void k_combination(T* __restrict__ psi, const typename Basis<T>::S* V, size_t ldv, int m,
-                              const double* __restrict__ c, uint64_t n) {
-    extern __shared__ float2 cs[];
-    for (int q = threadIdx.x; q < m; q += blockDim.x) {
-        float h, l;
-        split_f64(c[q], h, l);
-        cs[q] = make_float2(h, l);
-    }
-    __syncthreads();
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
-        float fs = 0.f, fc = 0.f, s = 0.f, cc = 0.f;
-        for (int j = 0; j < m; ++j) {
-            float vh, vl;
-            ld_basis(V + (size_t)j * ldv + i, vh, vl);
-            ff_mac(s, cc, vh, vl, cs[j].x, cs[j].y);
-            if ((j + 1) % kFlush == 0) {
-                ff_fold(fs, fc, s, cc);
-                s = cc = 0.f;
-            }
-        }
-        ff_fold(fs, fc, s, cc);
-        st_value(psi + i, fs, fc);
-    }
-}
 // Number of eigenvalues of the symmetric tridiagonal T (diagonal a, off-diagonal b) below x.
 static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, double x) {
     int cnt = 0;
@@ -874,10 +886,11 @@ struct Work {
     }
 };
 
-template <typename T>
+template <typename T, class P>
 static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int steps, int reorth, double* E0,
                        double* alpha_out, double* beta_out, int* steps_done, T* psi, cudaStream_t st) {
-    using S = typename Basis<T>::S;
+    using S = typename P::S;
+    using E = typename P::E;
     const uint64_t D = s->D;
     const size_t ldv = (D + 31) & ~(size_t)31;
     const int sms = sm_count_cached();
@@ -885,8 +898,8 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     if (!coop) return set_error(DQ_ECUDA, "Lanczos: the device does not support cooperative launches");
-    const size_t smem_max = (size_t)(steps + 1) * (sizeof(double) + sizeof(float2));
-    auto kern = k_lz_step<T>;
+    const size_t smem_max = (size_t)(steps + 1) * (sizeof(double) + sizeof(E));
+    auto kern = k_lz_step<T, P>;
     if (smem_max > 48 * 1024 &&
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) != cudaSuccess)
         return set_error(DQ_ECUDA, "Lanczos: shared memory for %d coefficients", steps + 1);
@@ -901,10 +914,10 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     if (!V) return rc;
     T* w = (T*)ws.get(ldv * sizeof(T), rc);
     if (!w) return rc;
-    float2* r = (float2*)ws.get(ldv * sizeof(float2), rc);
+    E* r = (E*)ws.get(ldv * sizeof(E), rc);
     if (!r) return rc;
-    double* x = nullptr;  // FP64 vectors: v_k in FP64, the product's input
-    if (sizeof(T) == 8 && !(x = (double*)ws.get(ldv * sizeof(double), rc))) return rc;
+    double* x = nullptr;  // v_k in FP64, the product's input, when the basis holds float pairs
+    if (P::kXBuffer && !(x = (double*)ws.get(ldv * sizeof(double), rc))) return rc;
     const size_t npart = (size_t)nb * (steps + 4) > (size_t)nbd ? (size_t)nb * (steps + 4) : (size_t)nbd;
     double* part = (double*)ws.get(npart * sizeof(double), rc);
     if (!part) return rc;
@@ -948,9 +961,9 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos start vector: %s", cudaGetErrorString(e));
     if (!(nrm2 > 0.0) || !std::isfinite(nrm2)) return set_error(DQ_EINVAL, "v0 has zero or non-finite norm");
-    k_lz_start<T><<<8 * sms, kRedThreads, 0, st>>>(V, x, v0, v0n, D);
+    k_lz_start<T, P><<<8 * sms, kRedThreads, 0, st>>>(V, x, v0, v0n, D);
 
-    LzStep<T> arg;
+    LzStep<T, P> arg;
     arg.ldv = ldv;
     arg.V = V;
     arg.w = w;
@@ -991,14 +1004,14 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
             if ((rc = consume(k - 2))) return rc;
             if (stop) break;
         }
-        const T* xk = sizeof(T) == 8 ? (const T*)x : (const T*)(V + (size_t)k * ldv);
+        const T* xk = P::kXBuffer ? (const T*)x : (const T*)(V + (size_t)k * ldv);
         int le = launch_matvec(s, t, xk, w, dtype, 1, st);
         if (le) return set_error(DQ_ECUDA, "matvec launch: %s", cudaGetErrorString((cudaError_t)le));
         arg.k = k;
         arg.vnext = k + 1 < steps ? V + (size_t)(k + 1) * ldv : nullptr;
         arg.xnext = x;
         void* args[] = {&arg};
-        const size_t smem = (size_t)(k + 1) * (sizeof(double) + sizeof(float2));
+        const size_t smem = (size_t)(k + 1) * (sizeof(double) + sizeof(E));
         e = cudaLaunchCooperativeKernel((const void*)kern, dim3(nb), dim3(kLzThreads), args, smem, st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos step launch: %s", cudaGetErrorString(e));
         cudaEventRecord(ws.events[k % 3], st);
@@ -1022,7 +1035,7 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
         std::vector<double> y = m == 1 ? std::vector<double>{1.0} : tridiag_eigvec(a, off, e0);
         e = cudaMemcpyAsync(hv, y.data(), m * sizeof(double), cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos Ritz vector: %s", cudaGetErrorString(e));
-        k_combination<T><<<8 * sms, kRedThreads, (size_t)m * sizeof(float2), st>>>(psi, V, ldv, m, hv, D);
+        k_combination<T, P><<<8 * sms, kRedThreads, (size_t)m * sizeof(E), st>>>(psi, V, ldv, m, hv, D);
         if ((rc = cuda_fail("Ritz vector"))) return rc;
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return set_error(DQ_ECUDA, "Lanczos: %s", cudaGetErrorString(e));
@@ -1046,11 +1059,19 @@ extern "C" int dq_lanczos(const dq_sector* s, const dq_terms* t, const void* v0,
     if (t->sector != s) return set_error(DQ_EINVAL, "terms were compiled for another sector");
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
     if (steps < 1 || steps > 4096) return set_error(DQ_EINVAL, "steps must be in [1, 4096]");
-    if (reorth < 0 || reorth > 2) return set_error(DQ_EINVAL, "reorth must be 0, 1 or 2");
+    const bool ds = (reorth & DQ_LZ_DOUBLE_SINGLE) != 0;
+    reorth &= ~DQ_LZ_DOUBLE_SINGLE;
+    if (reorth < 0 || reorth > 2) return set_error(DQ_EINVAL, "reorth must be 0, 1 or 2 (optionally | DQ_LZ_DOUBLE_SINGLE)");
     if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
     cudaStream_t st = (cudaStream_t)stream;
-    if (dtype == DQ_F64)
-        return run_lanczos<double>(s, t, (const double*)v0, steps, reorth, E0, alpha, beta, steps_done, (double*)psi,
-                                   st);
-    return run_lanczos<float>(s, t, (const float*)v0, steps, reorth, E0, alpha, beta, steps_done, (float*)psi, st);
+    if (dtype == DQ_F64) {
+        const double* v = (const double*)v0;
+        double* p = (double*)psi;
+        return ds ? run_lanczos<double, LzDS<double>>(s, t, v, steps, reorth, E0, alpha, beta, steps_done, p, st)
+                  : run_lanczos<double, LzF64<double>>(s, t, v, steps, reorth, E0, alpha, beta, steps_done, p, st);
+    }
+    const float* v = (const float*)v0;
+    float* p = (float*)psi;
+    return ds ? run_lanczos<float, LzDS<float>>(s, t, v, steps, reorth, E0, alpha, beta, steps_done, p, st)
+              : run_lanczos<float, LzF64<float>>(s, t, v, steps, reorth, E0, alpha, beta, steps_done, p, st);
 }
