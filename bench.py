@@ -39,11 +39,12 @@ FALLBACK_HBM = 6800.0
 # DRAM traffic per launch of the panel kernel from one ncu capture, keyed by the SHA-256 of the
 # panel kernel's sources (PANEL_SOURCES) it was taken on; reported only while they are unchanged.
 NCU_TRAFFIC = {
-    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum (one pass), k_panel on the full-size
-    # J1-J2 6x5 N = 15 product with FP64 vectors: 18.25 GB read + 1.31 GB written
-    ("j1j2_square_6x5_N15", 2, "f64", 1, "40f026dacd629da7"): 19.56e9,
-    # the same capture with FP32 vectors: 6.44 GB read + 0.61 GB written
-    ("j1j2_square_6x5_N15", 2, "f32", 1, "40f026dacd629da7"): 7.05e9,
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum (one pass),
+    # the fourth k_panel launch of the full-size J1-J2 6x5 N = 15 product with FP64 vectors:
+    # 17.63 GB read + 1.24 GB written
+    ("j1j2_square_6x5_N15", 2, "f64", 1, "221413569a1772bf"): 18.864e9,
+    # the same capture with FP32 vectors: 6.37 GB read + 0.61 GB written
+    ("j1j2_square_6x5_N15", 2, "f32", 1, "221413569a1772bf"): 6.984e9,
 }
 
 WORKLOADS = {
