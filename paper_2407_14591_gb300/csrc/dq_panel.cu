@@ -231,6 +231,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
     int u = 0;
     const int lead = pc.nx ? (nu < 2 ? nu : 2) : nu;  // units before the first cross partner
     for (; u < lead; ++u) run_unit(u);
+    int target = lead, frac = 0;
     // hops across the cut: panel s0 ^ bit_a of the neighbouring block, in the copy ring
     for (int j = 0; j < pc.nx; ++j) {
         const int s = 1 + j % (R - 1);
@@ -256,7 +257,12 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
             }
         }
         release_slot<XT, R>(s, j + R - 1, P, pc, X, smem, bstride, bar, lst, rg);
-        const int target = lead + (int)((long long)(nu - lead) * (j + 1) / pc.nx);
+        // target = lead + floor((nu - lead) (j + 1) / nx), kept incrementally
+        frac += nu - lead;
+        while (frac >= pc.nx) {
+            frac -= pc.nx;
+            ++target;
+        }
         for (; u < target; ++u) run_unit(u);
     }
     for (; u < nu; ++u) run_unit(u);
