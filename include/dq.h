@@ -169,7 +169,10 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
  * when the panel kernel's conditions on the coefficients fail but the structure fits (Q = 2, two
  * subsystems, P_1 of at most 13 sites and P_0 of at most 16, at most 64 bonds inside P_1, 64 across
  * the cut and 200 inside P_0, any coefficient per bond and per site). Terms made by
- * dq_make_cluster_terms report 2 (the cluster-merged kernel). */
+ * dq_make_cluster_terms report 2 (the cluster-merged kernel). *path = 4 for the warp-panel kernel:
+ * the panel kernel's conditions on the coefficients with three to eight subsystems, the last one
+ * of 8 to 10 sites and the others of at most 24 sites in all (panels of at most 252 rows, one
+ * warp each). */
 int dq_terms_path(const dq_terms* t, int* path);
 
 /* Compile terms in the cluster-merged form of App. C instead: the terms are grouped into clusters

@@ -159,7 +159,23 @@ struct PanelPlan {
     const uint32_t* list_off;
     const uint32_t* list_hdr;   // bits 0-7: class-0 P_0 partners, 8-15: class-1, 16-23: crossing
     const uint64_t* list;
-    const PanelDiag* diag;      // per panel, built on the host
+    const PanelDiag* diag;      // per panel, built on the host (two subsystems)
+    // three or more subsystems (the warp-panel kernel): prefix bits of the Sz Sz bonds across the
+    // cut, per class and per position b of P_1 (the per-panel counters are built on the device)
+    uint32_t xzA[kPanelMaxK][32];
+};
+
+// What the warp-panel kernel needs of the sector to rank a prefix pattern on the device: Eq.
+// (index) over the subsystems above the last one (at most kPWMaxSub subsystems in all).
+constexpr int kPWMaxSub = 8;
+struct PWRank {
+    int n_sub, N, L1, os_total;
+    int shift[kPWMaxSub], os_base[kPWMaxSub], os_ld[kPWMaxSub];
+    uint32_t fmask[kPWMaxSub];           // mask of P_k's field after the shift
+    const uint32_t* rank[kPWMaxSub];     // local index of every pattern of P_k
+    const uint64_t* off;                 // Eq. (offset) and Eq. (stride), os_total entries each
+    const uint64_t* str;
+    uint64_t D;
 };
 
 // Cluster-merged operator (App. C): every term lies in one cluster of at most kClMaxSites sites,
@@ -254,11 +270,13 @@ struct dq_terms {
     int max_hops;  // upper bound on off-diagonal elements per row
     bool panel_ok = false;     // the panel product applies (see PanelPlan)
     bool pb_ok = false;        // the per-bond panel product applies (PanelPB)
+    bool pw_ok = false;        // the warp-panel product applies (three or more subsystems, PanelPlan)
     dq::PanelPB pbp;
     bool cluster = false;      // cluster-merged form (App. C), dq_make_cluster_terms
     dq::DevTermsCL clv;
     std::vector<int> cl_sites; // host copy: the sites of each cluster, -1 after the last
     dq::PanelPlan pp;
+    dq::PWRank pwr;            // the warp-panel product's view of the sector
     void* scratch = nullptr;   // fixed-point copy of x and the exponent word, grown on demand
     size_t scratch_bytes = 0;
 };
@@ -299,6 +317,7 @@ int launch_cluster_matvec(const dq_sector* s, dq_terms* t, const void* x, void* 
 int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
                      const std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>>& pairs, dq_terms* t);
 int launch_panel_matvec(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
+int launch_panel_w(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
 size_t panel_scratch_bytes(const dq_sector* s, int dtype);
 int launch_panel_matvec_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* scratch,
                            void* stream);

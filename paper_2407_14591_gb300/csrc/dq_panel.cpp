@@ -11,6 +11,13 @@
 // Requirements: Q = 2, two subsystems, L_1 <= 15 (panels of at most 6435 rows), uniform
 // single-site fields, at most two distinct hop amplitudes and four distinct coefficients of
 // [s_i != s_j], and coefficients that are small integer multiples of one power of two.
+//
+// With three or more subsystems the same holds with P_0 = all subsystems but the last and P_1 =
+// the last one (Eq. (index): the last subsystem has offset 0 and stride 1 inside the block of its
+// particle number, so the rows sharing the prefix pattern s0 are again contiguous, in P_1's local
+// order). Those panels are small (P_1 of 8 to 10 sites: at most 252 rows) and many, so the
+// warp-panel kernel (dq_panel_w.cu) gives each panel one warp and ranks the partner panels on the
+// device; the host builds only the panel list and the bond tables.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -35,12 +42,83 @@ static int low_exponent(double v) {
     return e;
 }
 
+// The rest of the plan for three or more subsystems: the panel list (every prefix pattern s0
+// whose P_1 particle number N - |s0| fits, with its first index), the prefix masks
+// of the cut Sz Sz bonds per class and position b, the sector view for the device rank.
+static int build_panel_w(const dq_sector* s, PanelPlan& P, const std::vector<uint16_t>& t1rank,
+                         const std::vector<uint16_t>& t1states,
+                         const std::vector<std::pair<int, std::pair<uint32_t, uint32_t>>>& xz, dq_terms* t) {
+    const int L1 = P.L1, L0 = P.L0, N = P.N, last = s->n_sub - 1;
+    const int tl = s->dev.tab[last];
+    // panels grouped by length (the warps in flight then run one row-count variant of the
+    // kernel, which keeps its code in the instruction cache), in canonical order inside a group
+    std::vector<std::pair<std::pair<uint32_t, uint64_t>, uint32_t>> pl;  // ((length, start), s0)
+    int cmax = 0;
+    uint64_t smax = 0;
+    for (uint64_t s0 = 0; s0 < (1ull << L0); ++s0) {
+        const int n1 = N - __builtin_popcountll(s0);
+        if (n1 < 0 || n1 > L1) continue;
+        const uint32_t first = s->h.unrank_tab[tl][s->h.sec_start[tl][n1]];  // local index 0
+        const u128 w = ((u128)s0 << L1) | first;
+        const uint64_t st = host_rank(s, w);
+        pl.push_back({{P.t1len[n1], st}, (uint32_t)s0});
+        cmax = std::max(cmax, (int)P.t1len[n1]);
+        smax = std::max(smax, st);
+    }
+    std::sort(pl.begin(), pl.end());
+    if (pl.empty() || smax >> 48) return DQ_OK;
+    std::vector<uint32_t> ps0(pl.size());
+    std::vector<uint64_t> pst(pl.size());
+    for (size_t q = 0; q < pl.size(); ++q) {
+        pst[q] = pl[q].first.second;
+        ps0[q] = pl[q].second;
+    }
+    P.npanels = (uint32_t)pl.size();
+    P.cmax = cmax;
+    std::memset(P.xzA, 0, sizeof P.xzA);
+    for (auto& e : xz) P.xzA[e.first][__builtin_ctz(e.second.second)] |= e.second.first;
+    PWRank& R = t->pwr;
+    std::memset(&R, 0, sizeof R);
+    R.n_sub = s->n_sub;
+    R.N = N;
+    R.L1 = L1;
+    R.os_total = s->dev.os_total;
+    R.D = s->D;
+    for (int k = 0; k < s->n_sub; ++k) {
+        R.shift[k] = s->dev.shift[k];
+        R.os_base[k] = s->dev.os_base[k];
+        R.os_ld[k] = s->dev.os_ld[k];
+        R.fmask[k] = (uint32_t)((1ull << s->Lk[k]) - 1);
+        R.rank[k] = s->dev.rank_tab[s->dev.tab[k]];
+    }
+    R.off = s->dev.off;
+    R.str = s->dev.str;
+    int rc;
+    void* p;
+    if ((rc = dev_upload(t->dev_allocs, ps0.data(), ps0.size() * 4, &p))) return rc;
+    P.panel_s0 = (const uint32_t*)p;
+    if ((rc = dev_upload(t->dev_allocs, pst.data(), pst.size() * 8, &p))) return rc;
+    P.panel_start = (const uint64_t*)p;
+    if ((rc = dev_upload(t->dev_allocs, t1rank.data(), t1rank.size() * 2, &p))) return rc;
+    P.t1rank = (const uint16_t*)p;
+    if ((rc = dev_upload(t->dev_allocs, t1states.data(), t1states.size() * 2, &p))) return rc;
+    P.t1states = (const uint16_t*)p;
+    t->pw_ok = true;
+    return DQ_OK;
+}
+
 int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
                      const std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>>& pairs, dq_terms* t) {
     t->panel_ok = false;
-    if (s->Q != 2 || s->n_sub != 2 || !uniform_lin) return DQ_OK;
-    const int L0 = s->Lk[0], L1 = s->Lk[1], N = s->N;
-    if (L1 > 15 || L0 > 16 || L1 < 1) return DQ_OK;
+    t->pw_ok = false;
+    if (s->Q != 2 || s->n_sub < 2 || !uniform_lin || s->wide) return DQ_OK;
+    const bool warp = s->n_sub >= 3;
+    const int L1 = s->Lk[s->n_sub - 1], L0 = s->L - L1, N = s->N;
+    if (warp) {
+        if (s->n_sub > kPWMaxSub || L1 < 8 || L1 > 10 || L0 > 24) return DQ_OK;
+    } else if (L1 > 15 || L0 > 16 || L1 < 1) {
+        return DQ_OK;
+    }
     PanelPlan& P = t->pp;
     std::memset(&P, 0, sizeof P);
     P.L0 = L0;
@@ -183,9 +261,10 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
         if (!scaled(Avals[k], P.MA[k])) return DQ_OK;
     P.emin = emin;
     // P_1 tables (local index within its particle-number sector, and the states per sector)
-    const auto& rt = s->h.rank_tab[s->dev.tab[1]];
-    const auto& ut = s->h.unrank_tab[s->dev.tab[1]];
-    const auto& ss = s->h.sec_start[s->dev.tab[1]];
+    const int tl = s->dev.tab[s->n_sub - 1];
+    const auto& rt = s->h.rank_tab[tl];
+    const auto& ut = s->h.unrank_tab[tl];
+    const auto& ss = s->h.sec_start[tl];
     std::vector<uint16_t> t1rank(rt.size()), t1states(ut.size());
     for (size_t q = 0; q < rt.size(); ++q) t1rank[q] = (uint16_t)(rt[q] == 0xffffffffu ? 0 : rt[q]);
     for (size_t q = 0; q < ut.size(); ++q) t1states[q] = (uint16_t)ut[q];
@@ -193,6 +272,7 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
         P.t1start[n] = ss[n <= L1 ? n : L1 + 1];
         P.t1len[n] = n <= L1 ? ss[n + 1] - ss[n] : 0;
     }
+    if (warp) return build_panel_w(s, P, t1rank, t1states, xz, t);
     // panels in canonical order: particle number of P_0, then its local order
     std::vector<uint32_t> ps0;
     std::vector<uint64_t> pst;

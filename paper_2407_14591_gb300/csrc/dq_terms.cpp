@@ -164,7 +164,7 @@ static int compile_q2(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>> plist(pairs.begin(), pairs.end());
         int rc = build_panel_plan(s, C, uniform_lin, plist, t);
         if (rc) return rc;
-        if (!t->panel_ok && (rc = build_panel_pb(s, C_raw, lin, plist, t))) return rc;
+        if (!t->panel_ok && !t->pw_ok && (rc = build_panel_pb(s, C_raw, lin, plist, t))) return rc;
     }
     v.Cf = (float)v.C;
     // Fixed-point coefficients for FP64 vectors: one exponent emin for all of them, chosen so
@@ -468,7 +468,7 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
 int dq_terms_path(const dq_terms* t, int* path) {
     clear_error();
     if (!t || !path) return set_error(DQ_EINVAL, "NULL argument");
-    *path = t->cluster ? 2 : (t->panel_ok ? 1 : (t->pb_ok ? 3 : 0));
+    *path = t->cluster ? 2 : (t->panel_ok ? 1 : (t->pw_ok ? 4 : (t->pb_ok ? 3 : 0)));
     return DQ_OK;
 }
 
