@@ -34,6 +34,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -904,7 +905,11 @@ static int run_lanczos(const dq_sector* s, const dq_terms* t, const T* v0, int s
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max) != cudaSuccess)
         return set_error(DQ_ECUDA, "Lanczos: shared memory for %d coefficients", steps + 1);
     int per_sm = occupancy_cached(reinterpret_cast<const void*>(kern), kLzThreads, smem_max);
-    if (per_sm > 2) per_sm = 2;
+    // blocks per SM: two, or one for sectors below 4 M elements (fewer arrivals at each grid
+    // barrier and fewer partials to reduce; FP32 vectors with FP64 passes are the exception, they
+    // measured faster with two)
+    const int per_sm_max = D < (1ull << 22) && !std::is_same<P, LzF64<float>>::value ? 1 : 2;
+    if (per_sm > per_sm_max) per_sm = per_sm_max;
     if (per_sm < 1) return set_error(DQ_ECUDA, "Lanczos: the step kernel does not fit on an SM");
     const int nb = per_sm * sms;  // blocks of the cooperative step kernel (all resident)
     const int nbd = 2 * sms;      // blocks of the start-vector reduction
