@@ -170,9 +170,9 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
  * subsystems, P_1 of at most 13 sites and P_0 of at most 16, at most 64 bonds inside P_1, 64 across
  * the cut and 200 inside P_0, any coefficient per bond and per site). Terms made by
  * dq_make_cluster_terms report 2 (the cluster-merged kernel). *path = 4 for the warp-panel kernel:
- * the panel kernel's conditions on the coefficients with three to eight subsystems, the last one
- * of 8 to 10 sites and the others of at most 24 sites in all (panels of at most 252 rows, one
- * warp each). */
+ * the panel kernel's conditions on the coefficients with two to eight subsystems, the last one of
+ * 8 to 10 sites and the others of at most 24 sites in all (panels of at most 252 rows, one warp
+ * each; with two subsystems this replaces the panel kernel for such small panels). */
 int dq_terms_path(const dq_terms* t, int* path);
 
 /* Compile terms in the cluster-merged form of App. C instead: the terms are grouped into clusters
@@ -224,8 +224,8 @@ int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int
  * The scratch (a fixed-point copy of x and a small header) lives in a static device array of
  * 64 MiB that every GPU loading this library reserves until the process exits. Hence the limit:
  * D <= 8,388,568 for DQ_F64 and D <= 16,777,144 for DQ_F32; larger sectors return DQ_ERANGE with
- * the limit in dq_last_error(). Only terms on the panel path (dq_terms_path == 1) are served;
- * others return DQ_EINVAL. The first call on a device does a one-time set-up: it looks up the
+ * the limit in dq_last_error(). Only terms on the panel paths (dq_terms_path 1 or 4) are
+ * served; others return DQ_EINVAL. The first call on a device does a one-time set-up: it looks up the
  * array's device address (cudaGetSymbolAddress) and caches it. With CUDA's default lazy module
  * loading, that lookup is also when the runtime loads the code module holding the array, so the
  * 64 MiB are taken from the device at that first call, not when the library is loaded: make the

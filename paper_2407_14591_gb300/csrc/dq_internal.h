@@ -318,6 +318,8 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
                      const std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>>& pairs, dq_terms* t);
 int launch_panel_matvec(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
 int launch_panel_w(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
+int launch_panel_w_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,
+                      void* stream);
 size_t panel_scratch_bytes(const dq_sector* s, int dtype);
 int launch_panel_matvec_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* scratch,
                            void* stream);

@@ -1,8 +1,8 @@
-// dq_matvec_noalloc: the panel product with its scratch in a fixed, file-scope device array, for
-// callers that must not allocate device memory while they run (see include/dq.h).
+// dq_matvec_noalloc: the panel products with their scratch in a fixed, file-scope device array,
+// for callers that must not allocate device memory while they run (see include/dq.h).
 //
-// The scratch holds the workspace header and the fixed-point copy of x that the panel kernel
-// reads (dq_panel.cu). The array is static: it is reserved when the code module that holds it
+// The scratch holds the workspace header and the fixed-point copy of x that the panel kernels
+// read (dq_panel.cu, dq_panel_w.cu). The array is static: it is reserved when the code module that holds it
 // is loaded on a GPU and stays reserved until the process exits. Under CUDA's default lazy
 // module loading this file's module (it has no kernels of its own) is loaded by the first
 // cudaGetSymbolAddress on each device, i.e. inside the first dq_matvec_noalloc call there, which
@@ -55,8 +55,8 @@ extern "C" int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const vo
     if (t->sector != s) return set_error(DQ_EINVAL, "terms were compiled for another sector");
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
     if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
-    if (!t->panel_ok)
-        return set_error(DQ_EINVAL, "dq_matvec_noalloc serves only terms on the panel path (dq_terms_path == 1)");
+    if (!t->panel_ok && !t->pw_ok)
+        return set_error(DQ_EINVAL, "dq_matvec_noalloc serves only terms on the panel paths (dq_terms_path 1 or 4)");
     const size_t need = panel_scratch_bytes(s, dtype);
     if (need > kNoAllocScratchBytes)
         return set_error(DQ_ERANGE,
@@ -71,7 +71,8 @@ extern "C" int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const vo
     void* ws = nullptr;
     int rc = noalloc_scratch(&ws);
     if (rc) return rc;
-    int e = launch_panel_matvec_ws(s, t, x, y, dtype, ws, stream);
+    int e = t->panel_ok ? launch_panel_matvec_ws(s, t, x, y, dtype, ws, stream)
+                        : launch_panel_w_ws(s, t, x, y, dtype, ws, stream);
     if (e) return set_error(DQ_ECUDA, "matvec_noalloc launch: %s", cudaGetErrorString((cudaError_t)e));
     return DQ_OK;
 }

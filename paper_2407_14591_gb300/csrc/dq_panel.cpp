@@ -17,7 +17,8 @@
 // particle number, so the rows sharing the prefix pattern s0 are again contiguous, in P_1's local
 // order). Those panels are small (P_1 of 8 to 10 sites: at most 252 rows) and many, so the
 // warp-panel kernel (dq_panel_w.cu) gives each panel one warp and ranks the partner panels on the
-// device; the host builds only the panel list and the bond tables.
+// device; the host builds only the panel list and the bond tables. Two subsystems whose P_1 has 8
+// to 10 sites take that kernel too.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -112,7 +113,9 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
     t->panel_ok = false;
     t->pw_ok = false;
     if (s->Q != 2 || s->n_sub < 2 || !uniform_lin || s->wide) return DQ_OK;
-    const bool warp = s->n_sub >= 3;
+    // the warp-panel kernel for three or more subsystems, and for two when the panels are small
+    // (P_1 of 8 to 10 sites: at most 252 rows, which leave most of a 1024-thread CTA idle)
+    const bool warp = s->n_sub >= 3 || (s->Lk[s->n_sub - 1] >= 8 && s->Lk[s->n_sub - 1] <= 10);
     const int L1 = s->Lk[s->n_sub - 1], L0 = s->L - L1, N = s->N;
     if (warp) {
         if (s->n_sub > kPWMaxSub || L1 < 8 || L1 > 10 || L0 > 24) return DQ_OK;

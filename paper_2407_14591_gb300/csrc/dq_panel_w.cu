@@ -323,20 +323,12 @@ __global__ void __launch_bounds__(kPWT, 4) k_panel_w(PanelPlan P, PWRank R, cons
     }
 }
 
+// ws: the fixed-point scratch (header and X, panel_scratch_bytes).
 template <typename T, typename XT, int NA>
-static int run_pw(const dq_sector* s, dq_terms* t, const T* x, T* y, cudaStream_t st) {
+static int run_pw(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {
     const PanelPlan& P = t->pp;
-    const size_t need = panel_scratch_bytes(s, sizeof(T) == 8 ? DQ_F64 : DQ_F32);
-    if (t->scratch_bytes < need) {
-        if (t->scratch) cudaFree(t->scratch);
-        t->scratch = nullptr;
-        t->scratch_bytes = 0;
-        cudaError_t e = cudaMalloc(&t->scratch, need);
-        if (e != cudaSuccess) return (int)e;
-        t->scratch_bytes = need;
-    }
-    WsHeader* h = reinterpret_cast<WsHeader*>(t->scratch);
-    XT* X = reinterpret_cast<XT*>(reinterpret_cast<char*>(t->scratch) + 256);
+    WsHeader* h = reinterpret_cast<WsHeader*>(ws);
+    XT* X = reinterpret_cast<XT*>(reinterpret_cast<char*>(ws) + 256);
     cudaMemsetAsync(h, 0, sizeof(WsHeader), st);
     const int sms = sm_count_cached();
     k_exp_max<T><<<sms * 8, 256, 0, st>>>(x, s->D, h);
@@ -357,14 +349,28 @@ static int run_pw(const dq_sector* s, dq_terms* t, const T* x, T* y, cudaStream_
     return (int)cudaGetLastError();
 }
 
-int launch_panel_w(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream) {
+int launch_panel_w_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,
+                      void* stream) {
     cudaStream_t st = (cudaStream_t)stream;
     const bool two = t->pp.nA > 1;
     if (dtype == DQ_F64)
-        return two ? run_pw<double, long long, 2>(s, t, (const double*)x, (double*)y, st)
-                   : run_pw<double, long long, 1>(s, t, (const double*)x, (double*)y, st);
-    return two ? run_pw<float, int, 2>(s, t, (const float*)x, (float*)y, st)
-               : run_pw<float, int, 1>(s, t, (const float*)x, (float*)y, st);
+        return two ? run_pw<double, long long, 2>(s, t, (const double*)x, (double*)y, ws, st)
+                   : run_pw<double, long long, 1>(s, t, (const double*)x, (double*)y, ws, st);
+    return two ? run_pw<float, int, 2>(s, t, (const float*)x, (float*)y, ws, st)
+               : run_pw<float, int, 1>(s, t, (const float*)x, (float*)y, ws, st);
+}
+
+int launch_panel_w(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream) {
+    const size_t need = panel_scratch_bytes(s, dtype);
+    if (t->scratch_bytes < need) {
+        if (t->scratch) cudaFree(t->scratch);
+        t->scratch = nullptr;
+        t->scratch_bytes = 0;
+        cudaError_t e = cudaMalloc(&t->scratch, need);
+        if (e != cudaSuccess) return (int)e;
+        t->scratch_bytes = need;
+    }
+    return launch_panel_w_ws(s, t, x, y, dtype, t->scratch, stream);
 }
 
 }  // namespace dq

@@ -80,7 +80,7 @@ def test_general_nonfinite_input_gives_nan_and_error_word():
     s.check_device()
 
 
-@pytest.mark.parametrize("path", ["panel", "panel_pb", "general"])
+@pytest.mark.parametrize("path", ["panel", "panel_w", "panel_pb", "general"])
 def test_graded_column_elementwise_bound(path):
     """One column whose entries span twenty decades (|x_i| = 10^-20u, u ~ U[0, 1], random signs):
     every y_i meets the element-wise bound of the block fixed-point FP64 form,
@@ -88,8 +88,8 @@ def test_graded_column_elementwise_bound(path):
     n_i the nonzeros of row i, i.e. the error is absolute in units of the column maximum, not
     relative to |y_i|. The element-wise relative errors are printed for the record."""
     rng = np.random.default_rng(17)
-    L, N = 14, 7
-    if path == "panel":
+    L, N = (16, 4) if path == "panel_w" else (14, 7)  # D = 1820 or 3432: a dense H for the bound
+    if path in ("panel", "panel_w"):
         terms = wl.heisenberg_terms(wl.chain_bonds(L), 1.0, 1.0) + wl.field_terms(np.full(L, 0.375))
         n_sub = 2
     else:

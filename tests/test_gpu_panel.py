@@ -25,8 +25,8 @@ def j1j2_terms(Lx, Ly, J2=0.5, delta=1.0):
 def run_both(L, N, terms, n_sub=2, scale=1.0, seed=0, want_panel=True):
     s = b.make_sector(L, 2, N, n_sub)
     t = b.make_terms(s, terms)
-    if want_panel:
-        assert t.path == "panel"
+    if want_panel:  # the class-sum panel kernel, or its warp-per-panel form for P_1 of 8-10 sites
+        assert t.path == ("panel_w" if 8 <= s.partition[-1] <= 10 else "panel"), s.partition
     o = OracleSector(L, 2, N, partition=s.partition)
     x = np.random.default_rng(seed).uniform(-1, 1, o.dim) * scale
     ref = o_matvec(o, terms, x)
@@ -69,17 +69,21 @@ def test_mixed_kinds_uniform_field():
     check(*run_both(L, 7, terms, seed=3))
 
 
+@pytest.mark.parametrize("lat", [(4, 4), (11, 2)])  # P_1 of 8 sites (warp-panel), 11 sites (panel)
 @pytest.mark.parametrize("scale", [1e-200, 1e-30, 1e30, 1e200])
-def test_extreme_scales(scale):
-    terms = j1j2_terms(4, 4)
-    y, ref, _, _ = run_both(16, 8, terms, scale=scale, seed=9)
+def test_extreme_scales(scale, lat):
+    terms = j1j2_terms(*lat)
+    L = lat[0] * lat[1]
+    y, ref, _, _ = run_both(L, L // 2, terms, scale=scale, seed=9)
     assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
 
 
-def test_zero_and_nonfinite_input():
-    s = b.make_sector(16, 2, 8, 2)
-    t = b.make_terms(s, j1j2_terms(4, 4))
-    assert t.path == "panel"
+@pytest.mark.parametrize("lat,path", [((4, 4), "panel_w"), ((11, 2), "panel")])
+def test_zero_and_nonfinite_input(lat, path):
+    L = lat[0] * lat[1]
+    s = b.make_sector(L, 2, L // 2, 2)
+    t = b.make_terms(s, j1j2_terms(*lat))
+    assert t.path == path
     x = torch.zeros(s.dim, dtype=torch.float64, device=DEV)
     y = b.matvec(s, t, x)
     torch.cuda.synchronize()
@@ -126,12 +130,12 @@ def test_repeated_calls_and_two_terms_objects():
 
 
 def test_timing_hooks_count_and_time_the_main_kernel():
-    """dq_timing_*: three kernels per product on both panel paths (two prepass kernels and the
-    class-sum or the per-bond panel kernel), positive times."""
+    """dq_timing_*: three kernels per product on the panel paths (two prepass kernels and the
+    warp-panel or the per-bond panel kernel), positive times."""
     s = b.make_sector(20, 2, 10, 2)
     terms = wl.heisenberg_terms(wl.chain_bonds(20), 1.0, 1.0)
     tp = b.make_terms(s, terms)
-    assert tp.path == "panel"
+    assert tp.path == "panel_w"
     tg = b.make_terms(s, terms + [("Z", 3, -1, 0.3)])  # a non-uniform field: the per-bond panel path
     assert tg.path == "panel_pb"
     x = torch.rand(s.dim, dtype=torch.float64, device=DEV)
@@ -152,9 +156,11 @@ def test_timing_hooks_count_and_time_the_main_kernel():
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_products_replay_from_a_cuda_graph(dtype):
     """dq_matvec captured in a CUDA graph (after one eager call has set up its scratch) gives,
-    on replay with new x, exactly what an eager call gives: panel path and general path."""
+    on replay with new x, exactly what an eager call gives: the warp-panel, panel and general
+    paths."""
     rng = np.random.default_rng(12)
-    cases = [(b.make_sector(20, 2, 10, 2), wl.heisenberg_terms(wl.chain_bonds(20), 1.0, 1.0), "panel"),
+    cases = [(b.make_sector(20, 2, 10, 2), wl.heisenberg_terms(wl.chain_bonds(20), 1.0, 1.0), "panel_w"),
+             (b.make_sector(22, 2, 11, 2), wl.heisenberg_terms(wl.chain_bonds(22), 1.0, 1.0), "panel"),
              (b.make_sector(14, 2, 7, 3), wl.heisenberg_terms(wl.chain_bonds(14), rng.uniform(0.5, 1.5, 14), 1.0)
               + wl.field_terms(rng.uniform(-3, 3, 14)), "general")]
     for s, terms, path in cases:

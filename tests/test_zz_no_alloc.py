@@ -22,12 +22,15 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def test_noalloc_matches_matvec_on_two_calls():
-    """Two calls in a row, each against dq_matvec on the same input (FP64 bar 1e-12, FP32 1e-5)."""
-    s = b.make_sector(20, 2, 10, 2)  # D = 184,756
-    nn, nnn = wl.square_bonds(5, 4)
+@pytest.mark.parametrize("lat,path", [((5, 4), "panel_w"), ((11, 2), "panel")])
+def test_noalloc_matches_matvec_on_two_calls(lat, path):
+    """Two calls in a row, each against dq_matvec on the same input (FP64 bar 1e-12, FP32 1e-5),
+    on both panel paths (D = 184,756 and 705,432)."""
+    L = lat[0] * lat[1]
+    s = b.make_sector(L, 2, L // 2, 2)
+    nn, nnn = wl.square_bonds(*lat)
     t = b.make_terms(s, wl.heisenberg_terms(nn, 1.0) + wl.heisenberg_terms(nnn, 0.5))
-    assert t.path == "panel"
+    assert t.path == path
     lib = b.lib()
     rng = np.random.default_rng(20240719)
     for call in range(2):
@@ -74,7 +77,7 @@ def test_noalloc_call_takes_no_device_memory():
     b.matvec_noalloc(s0, t0, x0, torch.empty_like(x0))  # set-up (and kernel load) on this device
     s = b.make_sector(16, 2, 7, 2)
     t = b.make_terms(s, terms)
-    assert t.path == "panel"
+    assert t.path == "panel_w"
     x = torch.rand(s.dim, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     ref = b.matvec(s, t, x, torch.empty_like(x))
