@@ -161,9 +161,11 @@ int dq_check_device(const dq_sector* s, void* stream);
 int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_terms** out);
 
 /* Which product kernel dq_matvec uses for these terms with one right-hand side: *path = 1 for the
- * panel kernel (Q = 2, two subsystems, subsystem P_1 of at most 15 sites, uniform single-site
- * fields, at most two distinct hop amplitudes and four distinct Sz Sz coefficients, dyadic
- * coefficients), 0 for the general kernels (any Q, partition and nrhs). Both sum exactly in fixed
+ * panel kernel (Q = 2, uniform single-site fields, at most two distinct hop amplitudes and four
+ * distinct Sz Sz coefficients, dyadic coefficients; either two subsystems with P_1 of at most 15
+ * sites and P_0 of at most 16, or three or more subsystems whose last one has fewer than 8 or more
+ * than 10 sites, with P_1 = the last two subsystems, at most 15 sites, and the others at most 22
+ * sites in all), 0 for the general kernels (any Q, partition and nrhs). Both sum exactly in fixed
  * point (see dq_matvec) and compute the same y up to the rounding of the coefficients to their
  * integer grid, which is exact on the panel path. *path = 3 for the per-bond panel kernel, taken
  * when the panel kernel's conditions on the coefficients fail but the structure fits (Q = 2, two

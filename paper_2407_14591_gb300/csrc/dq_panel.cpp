@@ -19,6 +19,14 @@
 // warp-panel kernel (dq_panel_w.cu) gives each panel one warp and ranks the partner panels on the
 // device; the host builds only the panel list and the bond tables. Two subsystems whose P_1 has 8
 // to 10 sites take that kernel too.
+//
+// Three or more subsystems whose last one is shorter than 8 (or longer than 10) sites use P_1 =
+// the last TWO subsystems (the "tail") in the panel kernel instead: with the prefix pattern s0
+// fixed, the canonical key (n_0, σ0, ..., n_{n-2}, σ_{n-2}, n_{n-1}, σ_{n-1}) leaves only the
+// tail's two entries free, so those rows are again one contiguous range, ordered by the tail's
+// own two-subsystem canonical order (Eq. (index) restricted to the tail). That order depends on
+// the tail's particle number only; the host tabulates it (tail pattern -> local index) from the
+// sector's own rank and checks every panel's first and last row.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -115,11 +123,13 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
     if (s->Q != 2 || s->n_sub < 2 || !uniform_lin || s->wide) return DQ_OK;
     // the warp-panel kernel for three or more subsystems, and for two when the panels are small
     // (P_1 of 8 to 10 sites: at most 252 rows, which leave most of a 1024-thread CTA idle)
-    const bool warp = s->n_sub >= 3 || (s->Lk[s->n_sub - 1] >= 8 && s->Lk[s->n_sub - 1] <= 10);
-    const int L1 = s->Lk[s->n_sub - 1], L0 = s->L - L1, N = s->N;
+    const int ns = s->n_sub;
+    const bool warp = s->Lk[ns - 1] >= 8 && s->Lk[ns - 1] <= 10;
+    const bool tail = ns >= 3 && !warp;  // P_1 = the last two subsystems
+    const int L1 = tail ? s->Lk[ns - 2] + s->Lk[ns - 1] : s->Lk[ns - 1], L0 = s->L - L1, N = s->N;
     if (warp) {
-        if (s->n_sub > kPWMaxSub || L1 < 8 || L1 > 10 || L0 > 24) return DQ_OK;
-    } else if (L1 > 15 || L0 > 16 || L1 < 1) {
+        if (ns > kPWMaxSub || L0 > 24) return DQ_OK;
+    } else if (L1 > 15 || L1 < 1 || L0 > (tail ? 22 : 16)) {
         return DQ_OK;
     }
     PanelPlan& P = t->pp;
@@ -264,34 +274,97 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
         if (!scaled(Avals[k], P.MA[k])) return DQ_OK;
     P.emin = emin;
     // P_1 tables (local index within its particle-number sector, and the states per sector)
-    const int tl = s->dev.tab[s->n_sub - 1];
-    const auto& rt = s->h.rank_tab[tl];
-    const auto& ut = s->h.unrank_tab[tl];
-    const auto& ss = s->h.sec_start[tl];
-    std::vector<uint16_t> t1rank(rt.size()), t1states(ut.size());
-    for (size_t q = 0; q < rt.size(); ++q) t1rank[q] = (uint16_t)(rt[q] == 0xffffffffu ? 0 : rt[q]);
-    for (size_t q = 0; q < ut.size(); ++q) t1states[q] = (uint16_t)ut[q];
-    for (int n = 0; n <= L1 + 1 && n < 18; ++n) {
-        P.t1start[n] = ss[n <= L1 ? n : L1 + 1];
-        P.t1len[n] = n <= L1 ? ss[n + 1] - ss[n] : 0;
+    std::vector<uint16_t> t1rank, t1states;
+    if (!tail) {
+        const int tl = s->dev.tab[ns - 1];
+        const auto& rt = s->h.rank_tab[tl];
+        const auto& ut = s->h.unrank_tab[tl];
+        const auto& ss = s->h.sec_start[tl];
+        t1rank.resize(rt.size());
+        t1states.resize(ut.size());
+        for (size_t q = 0; q < rt.size(); ++q) t1rank[q] = (uint16_t)(rt[q] == 0xffffffffu ? 0 : rt[q]);
+        for (size_t q = 0; q < ut.size(); ++q) t1states[q] = (uint16_t)ut[q];
+        for (int n = 0; n <= L1 + 1 && n < 18; ++n) {
+            P.t1start[n] = ss[n <= L1 ? n : L1 + 1];
+            P.t1len[n] = n <= L1 ? ss[n + 1] - ss[n] : 0;
+        }
+    } else {
+        // the tail's order per particle number n: rank the tail patterns behind one prefix s0
+        // with |s0| = N - n and subtract the smallest index
+        t1rank.assign((size_t)1 << L1, 0);
+        t1states.assign((size_t)1 << L1, 0);
+        std::vector<std::vector<uint32_t>> byn(L1 + 1);
+        for (uint32_t w = 0; w < (1u << L1); ++w) byn[__builtin_popcount(w)].push_back(w);
+        uint32_t at = 0;
+        for (int n = 0; n <= L1 + 1 && n < 18; ++n) {
+            P.t1start[n] = at;
+            P.t1len[n] = 0;
+            if (n > L1) continue;
+            const int n0 = N - n;
+            if (n0 >= 0 && n0 <= L0) {
+                const u128 rep = (u128)((1ull << n0) - 1) << L1;
+                std::vector<uint64_t> r(byn[n].size());
+                uint64_t lo = UINT64_MAX;
+                for (size_t q = 0; q < byn[n].size(); ++q) lo = std::min(lo, r[q] = host_rank(s, rep | byn[n][q]));
+                std::vector<char> hit(byn[n].size(), 0);
+                for (size_t q = 0; q < byn[n].size(); ++q) {
+                    const uint64_t c = r[q] - lo;
+                    if (c >= byn[n].size() || hit[c]) return DQ_OK;  // not a contiguous range
+                    hit[c] = 1;
+                    t1rank[byn[n][q]] = (uint16_t)c;
+                    t1states[at + c] = (uint16_t)byn[n][q];
+                }
+            } else {
+                for (size_t q = 0; q < byn[n].size(); ++q) {
+                    t1rank[byn[n][q]] = (uint16_t)q;
+                    t1states[at + q] = (uint16_t)byn[n][q];
+                }
+            }
+            P.t1len[n] = (uint32_t)byn[n].size();
+            at += P.t1len[n];
+        }
     }
     if (warp) return build_panel_w(s, P, t1rank, t1states, xz, t);
     // panels in canonical order: particle number of P_0, then its local order
     std::vector<uint32_t> ps0;
     std::vector<uint64_t> pst;
-    const auto& u0 = s->h.unrank_tab[s->dev.tab[0]];
-    const auto& s0s = s->h.sec_start[s->dev.tab[0]];
     int cmax = 0;
-    for (int n0 = 0; n0 <= L0; ++n0) {
-        int n1 = N - n0;
-        if (n1 < 0 || n1 > L1) continue;
-        for (uint32_t q = s0s[n0]; q < s0s[n0 + 1]; ++q) {
-            uint32_t p = u0[q];
-            ps0.push_back(p);
-            pst.push_back(s->h.c0_tab[p]);
+    std::vector<uint64_t> tail_start;  // first index of every prefix pattern's panel (tail form)
+    if (!tail) {
+        const auto& u0 = s->h.unrank_tab[s->dev.tab[0]];
+        const auto& s0s = s->h.sec_start[s->dev.tab[0]];
+        for (int n0 = 0; n0 <= L0; ++n0) {
+            int n1 = N - n0;
+            if (n1 < 0 || n1 > L1) continue;
+            for (uint32_t q = s0s[n0]; q < s0s[n0 + 1]; ++q) {
+                uint32_t p = u0[q];
+                ps0.push_back(p);
+                pst.push_back(s->h.c0_tab[p]);
+            }
+            cmax = std::max(cmax, (int)P.t1len[n1]);
         }
-        cmax = std::max(cmax, (int)P.t1len[n1]);
+    } else {
+        tail_start.assign((size_t)1 << L0, UINT64_MAX);
+        std::vector<std::pair<uint64_t, uint32_t>> pl;
+        for (uint32_t s0 = 0; s0 < (1u << L0); ++s0) {
+            const int n1 = N - __builtin_popcount(s0);
+            if (n1 < 0 || n1 > L1) continue;
+            const u128 w = (u128)s0 << L1;
+            const uint32_t C1 = P.t1len[n1];
+            const uint64_t st = host_rank(s, w | t1states[P.t1start[n1]]);
+            // the panel is the contiguous range [st, st + C1) in the tail's order
+            if (host_rank(s, w | t1states[P.t1start[n1] + C1 - 1]) != st + C1 - 1) return DQ_OK;
+            tail_start[s0] = st;
+            pl.push_back({st, s0});
+            cmax = std::max(cmax, (int)C1);
+        }
+        std::sort(pl.begin(), pl.end());
+        for (auto& e : pl) {
+            ps0.push_back(e.second);
+            pst.push_back(e.first);
+        }
     }
+    auto start_of = [&](uint32_t p) -> uint64_t { return tail ? tail_start[p] : s->h.c0_tab[p]; };
     P.npanels = (uint32_t)ps0.size();
     P.cmax = cmax;
     // per-panel diagonal counters (see PanelDiag)
@@ -330,12 +403,12 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
             for (int l = (k ? P.p0_end[k - 1] : 0); l < P.p0_end[k]; ++l) {
                 uint32_t m = P.p0_mask[l];
                 if (__builtin_popcount(s0 & m) != 1) continue;
-                lst.push_back(s->h.c0_tab[s0 ^ m]);
+                lst.push_back(start_of(s0 ^ m));
                 ++cnt[k];
             }
         uint32_t nx = 0;
         for (int g = 0; g < P.n_xg; ++g) {
-            uint64_t src = s->h.c0_tab[s0 ^ P.xg_abit[g]];
+            uint64_t src = start_of(s0 ^ P.xg_abit[g]);
             if (src == UINT64_MAX) continue;
             if (src >> 48) return DQ_OK;  // indices this large are left to the general kernel
             lst.push_back(src | ((uint64_t)g << 48));

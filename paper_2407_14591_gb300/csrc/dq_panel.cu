@@ -27,7 +27,10 @@
 
 namespace dq {
 
-constexpr int kPT = 1024;  // threads per panel CTA
+// threads per panel CTA: 1024 (one CTA per SM) for panels of more than 1024 rows, else 512 (two
+// CTAs per SM, each thread on at most two rows)
+constexpr int kPT = 1024;
+constexpr int kPTSmall = 512;
 constexpr unsigned kWaitLimit = 1u << 22;
 
 // ------------------------------------------------------------------ mbarrier / bulk copy -----
@@ -145,14 +148,14 @@ __device__ __forceinline__ void issue_cut(int j, int s, const PanelPlan& P, cons
 // Every warp calls this when it has finished reading slot s; the last of the block's warps
 // starts the copy of cut partner jn into it (if there is one). No block-wide barrier: the other
 // warps go on with their next slot.
-template <typename XT, int R>
+template <typename XT, int R, int NT>
 __device__ __forceinline__ void release_slot(int s, int jn, const PanelPlan& P, const PanelCtx& pc, const XT* X,
                                              unsigned char* smem, size_t bstride, uint64_t* bar, const uint64_t* lst,
                                              Ring<R>& rg) {
     __syncwarp();
     if ((threadIdx.x & 31) == 0) {
         __threadfence_block();  // this warp's reads of the slot happen before the count
-        if (atomicAdd(&rg.done[s], 1) == kPT / 32 - 1) {
+        if (atomicAdd(&rg.done[s], 1) == NT / 32 - 1) {
             rg.done[s] = 0;
             __threadfence_block();
             if (jn < pc.nx && !rg.abort) issue_cut<XT, R>(jn, s, P, pc, X, smem, bstride, bar, lst, rg);
@@ -160,9 +163,9 @@ __device__ __forceinline__ void release_slot(int s, int jn, const PanelPlan& P, 
     }
 }
 
-// All the work of one panel for rows tid + e * kPT, e < E. Rows past the panel hold s = 0: their
+// All the work of one panel for rows tid + e * NT, e < E. Rows past the panel hold s = 0: their
 // gathers read in-range entries, and they are never stored.
-template <typename XT, typename OUT, int NA, int R, int E>
+template <typename XT, typename OUT, int NA, int R, int E, int NT>
 __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restrict__ X, OUT* __restrict__ y,
                                            unsigned char* smem, uint64_t* bar, const uint64_t* lst, const PanelDiag& dg,
                                            const PanelCtx& pc, size_t bstride, uint32_t& ph, int scale, int& fail,
@@ -174,7 +177,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
     const uint16_t* st = P.t1states + P.t1start[pc.n1];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        int c = tid + e * kPT;
+        int c = tid + e * NT;
         s2[e] = c < pc.C ? ((uint32_t)__ldg(st + c) << 1) : 0u;
 #pragma unroll
         for (int k = 0; k < NA; ++k) acc[k][e] = 0;
@@ -182,24 +185,52 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
     // The work of the panel in units that need no copy: P_0 partner panels two at a time (per
     // amplitude class), and P_1 bond layers. They are interleaved with the cross partners of
     // the copy ring, so that each bulk copy lands while the warps work on units.
-    const int n0a = (pc.ncls0 + 1) >> 1;                // class-0 P_0 units
-    const int n0u = n0a + ((pc.np0 - pc.ncls0 + 1) >> 1);  // all P_0 units
+    // P_0 partner panels per unit: two, or four when a thread has at most two rows (more loads
+    // in flight per thread)
+    constexpr int kP0 = NT == kPT ? 2 : 4;
+    const int n0a = (pc.ncls0 + kP0 - 1) / kP0;                  // class-0 P_0 units
+    const int n0u = n0a + (pc.np0 - pc.ncls0 + kP0 - 1) / kP0;  // all P_0 units
     const int nu = n0u + P.n_p1l;
     auto p0_unit = [&](auto kc, int l, int l1) {
         constexpr int k = decltype(kc)::value;
-        if (l + 1 < l1) {
+        if constexpr (kP0 != 2) {
+            if (l + kP0 <= l1) {
+                const XT* src[kP0];
+#pragma unroll
+                for (int q = 0; q < kP0; ++q) src[q] = X + lst[l + q];
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int c = tid + e * NT;
+                    if (c < pc.C) {
+                        long long a = 0;
+#pragma unroll
+                        for (int q = 0; q < kP0; ++q) a += (long long)__ldg(src[q] + c);
+                        acc[k][e] += a;
+                    }
+                }
+            } else {
+                for (; l < l1; ++l) {
+                    const XT* src = X + lst[l];
+#pragma unroll
+                    for (int e = 0; e < E; ++e) {
+                        const int c = tid + e * NT;
+                        if (c < pc.C) acc[k][e] += (long long)__ldg(src + c);
+                    }
+                }
+            }
+        } else if (l + 1 < l1) {
             const XT* src = X + lst[l];
             const XT* src2 = X + lst[l + 1];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int c = tid + e * kPT;
+                const int c = tid + e * NT;
                 if (c < pc.C) acc[k][e] += (long long)__ldg(src + c) + (long long)__ldg(src2 + c);
             }
         } else {
             const XT* src = X + lst[l];
 #pragma unroll
             for (int e = 0; e < E; ++e) {
-                const int c = tid + e * kPT;
+                const int c = tid + e * NT;
                 if (c < pc.C) acc[k][e] += (long long)__ldg(src + c);
             }
         }
@@ -209,9 +240,9 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
     // conflicts and no branch)
     auto run_unit = [&](int u) {
         if (u < n0a) {
-            p0_unit(std::integral_constant<int, 0>(), 2 * u, pc.ncls0);
+            p0_unit(std::integral_constant<int, 0>(), kP0 * u, pc.ncls0);
         } else if (u < n0u) {
-            if constexpr (NA > 1) p0_unit(std::integral_constant<int, NA - 1>(), pc.ncls0 + 2 * (u - n0a), pc.np0);
+            if constexpr (NA > 1) p0_unit(std::integral_constant<int, NA - 1>(), pc.ncls0 + kP0 * (u - n0a), pc.np0);
         } else {
             const int l = u - n0u, d = P.p1l_d[l];
 #pragma unroll
@@ -256,7 +287,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
                 }
             }
         }
-        release_slot<XT, R>(s, j + R - 1, P, pc, X, smem, bstride, bar, lst, rg);
+        release_slot<XT, R, NT>(s, j + R - 1, P, pc, X, smem, bstride, bar, lst, rg);
         // target = lead + floor((nu - lead) (j + 1) / nx), kept incrementally
         frac += nu - lead;
         while (frac >= pc.nx) {
@@ -270,7 +301,7 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
     const uint32_t m1 = (1u << P.L1) - 1u;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        int c = tid + e * kPT;
+        int c = tid + e * NT;
         if (c >= pc.C) continue;
         const uint32_t s = s2[e] >> 1;
         long long md = P.MC;
@@ -292,8 +323,8 @@ __device__ __forceinline__ void panel_rows(const PanelPlan& P, const XT* __restr
     }
 }
 
-template <typename XT, typename OUT, int NA, int R>
-__global__ void __launch_bounds__(kPT, 1)
+template <typename XT, typename OUT, int NA, int R, int NT>
+__global__ void __launch_bounds__(NT, kPT / NT)
     k_panel(PanelPlan P, const XT* __restrict__ X, OUT* __restrict__ y, const WsHeader* __restrict__ h, int* err,
             int cap) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -323,13 +354,13 @@ __global__ void __launch_bounds__(kPT, 1)
         t1[kT1Entries] = zoff;
     }
     if (tid < kZeroPad * R) reinterpret_cast<XT*>(smem + kOwn + (tid / kZeroPad) * bstride)[cap - 1 + tid % kZeroPad] = 0;
-    for (int q = tid; q < (1 << P.L1); q += kPT) t1[q] = (uint16_t)(__ldg(P.t1rank + q) * sizeof(XT));
+    for (int q = tid; q < (1 << P.L1); q += NT) t1[q] = (uint16_t)(__ldg(P.t1rank + q) * sizeof(XT));
     __syncthreads();
     if (h->bad) {  // an Inf or NaN in x: y is NaN and the error word is raised
         for (uint32_t pi = blockIdx.x; pi < P.npanels; pi += gridDim.x) {
             const uint64_t st = P.panel_start[pi];
             const int C = (int)P.t1len[P.N - __popc(P.panel_s0[pi])];
-            for (int c = tid; c < C; c += kPT) y[st + c] = (OUT)NAN;
+            for (int c = tid; c < C; c += NT) y[st + c] = (OUT)NAN;
         }
         if (blockIdx.x == 0 && tid == 0) atomicAdd(err, 1);
         return;
@@ -365,22 +396,30 @@ __global__ void __launch_bounds__(kPT, 1)
         // the panel's own x: plain coalesced loads into slot 0 (element c at kOwn + c*size)
         {
             const XT* src = X + pc.start;
-            for (int c = tid; c < pc.C; c += kPT) own[c] = __ldg(src + c);
+            for (int c = tid; c < pc.C; c += NT) own[c] = __ldg(src + c);
         }
         __syncthreads();
         const uint32_t hd = s_hdr;
         pc.ncls0 = (int)(hd & 255u);
         pc.np0 = pc.ncls0 + (int)((hd >> 8) & 255u);
         pc.nx = (int)((hd >> 16) & 255u);
-        // rows per thread: the smallest E with E * kPT >= C (every E from 1 to 7 is compiled)
-        switch ((pc.C + kPT - 1) / kPT) {
-            case 7: panel_rows<XT, OUT, NA, R, 7>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
-            case 6: panel_rows<XT, OUT, NA, R, 6>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
-            case 5: panel_rows<XT, OUT, NA, R, 5>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
-            case 4: panel_rows<XT, OUT, NA, R, 4>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
-            case 3: panel_rows<XT, OUT, NA, R, 3>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
-            case 2: panel_rows<XT, OUT, NA, R, 2>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
-            default: panel_rows<XT, OUT, NA, R, 1>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
+        // rows per thread: the smallest E with E * NT >= C (every E from 1 to 7 is compiled for
+        // 1024 threads; 512-thread CTAs take panels of at most 1024 rows)
+        if constexpr (NT == kPT) {
+            switch ((pc.C + NT - 1) / NT) {
+                case 7: panel_rows<XT, OUT, NA, R, 7, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+                case 6: panel_rows<XT, OUT, NA, R, 6, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+                case 5: panel_rows<XT, OUT, NA, R, 5, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+                case 4: panel_rows<XT, OUT, NA, R, 4, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+                case 3: panel_rows<XT, OUT, NA, R, 3, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+                case 2: panel_rows<XT, OUT, NA, R, 2, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg); break;
+                default: panel_rows<XT, OUT, NA, R, 1, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
+            }
+        } else {
+            if (pc.C > NT)
+                panel_rows<XT, OUT, NA, R, 2, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
+            else
+                panel_rows<XT, OUT, NA, R, 1, NT>(P, X, y, smem, bar, lst, dg, pc, bstride, ph, scale, fail, rg);
         }
         __syncthreads();
     }
@@ -405,7 +444,7 @@ size_t panel_scratch_bytes(const dq_sector* s, int dtype) {
 
 static int sms_count() { return sm_count_cached(); }
 
-template <typename T, typename XT, int NA, int R>
+template <typename T, typename XT, int NA, int R, int NT>
 static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {
     const PanelPlan& P = t->pp;
     WsHeader* h = reinterpret_cast<WsHeader*>(ws);
@@ -416,12 +455,16 @@ static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, vo
     k_to_fixed<T, XT><<<sms * 8, 256, 0, st>>>(x, X, s->D, h);
     const int cap = P.cmax + 16 / (int)sizeof(XT) + 4;
     size_t sm = PanelSmem<XT>::total(cap, R);
-    auto kern = k_panel<XT, T, NA, R>;
+    auto kern = k_panel<XT, T, NA, R, NT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return (int)e;
-    unsigned grid = (unsigned)(P.npanels < (uint32_t)sms ? P.npanels : (uint32_t)sms);
+    int per_sm = 1;
+    if (NT != kPT && (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, sm)) != cudaSuccess) return (int)e;
+    if (per_sm < 1) per_sm = 1;
+    const uint32_t slots = (uint32_t)sms * (uint32_t)per_sm;
+    unsigned grid = (unsigned)(P.npanels < slots ? P.npanels : slots);
     const int tslot = timing_start(st);
-    kern<<<grid, kPT, sm, st>>>(P, X, y, h, s->dev.err, cap);
+    kern<<<grid, NT, sm, st>>>(P, X, y, h, s->dev.err, cap);
     timing_stop(tslot, st, 3);
     return (int)cudaGetLastError();
 }
@@ -429,8 +472,15 @@ static int run_panel(const dq_sector* s, const dq_terms* t, const T* x, T* y, vo
 template <typename T, typename XT, int NA>
 static int run_panel_n(const dq_sector* s, const dq_terms* t, const T* x, T* y, void* ws, cudaStream_t st) {
     // copy slots (the panel's own buffer and the staging buffers) that fit next to the rank
-    // table in 227 KB of shared memory
-    return run_panel<T, XT, NA, sizeof(XT) == 8 ? 3 : 6>(s, t, x, y, ws, st);
+    // table in 227 KB of shared memory; panels of at most 1024 rows run two 512-thread CTAs per
+    // SM, with six slots when two such CTAs still fit in one SM's shared memory
+    if (t->pp.cmax <= 2 * kPTSmall) {
+        const int cap = t->pp.cmax + 16 / (int)sizeof(XT) + 4;
+        if (2 * (PanelSmem<XT>::total(cap, 6) + 2048) <= 232448)
+            return run_panel<T, XT, NA, 6, kPTSmall>(s, t, x, y, ws, st);
+        return run_panel<T, XT, NA, 3, kPTSmall>(s, t, x, y, ws, st);
+    }
+    return run_panel<T, XT, NA, sizeof(XT) == 8 ? 3 : 6, kPT>(s, t, x, y, ws, st);
 }
 
 int launch_panel_matvec_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,

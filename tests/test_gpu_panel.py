@@ -99,14 +99,16 @@ def test_zero_and_nonfinite_input(lat, path):
 
 def test_disorder_takes_the_per_bond_panel_kernel():
     """Per-bond couplings leave the class-sum panel kernel for the per-bond one (P_1 of at most 13
-    sites); three subsystems take the general kernel."""
+    sites); with three subsystems they take the general kernel, and uniform couplings with three
+    subsystems of 6, 5 and 5 sites the panel kernel with a tail of two."""
     L = 16
     J = np.random.default_rng(1).uniform(0.5, 1.5, L)
     terms = wl.heisenberg_terms(wl.chain_bonds(L), J)
     s = b.make_sector(L, 2, 8, 2)
     assert b.make_terms(s, terms).path == "panel_pb"
     s3 = b.make_sector(L, 2, 8, 3)
-    assert b.make_terms(s3, wl.heisenberg_terms(wl.chain_bonds(L), 1.0)).path == "general"
+    assert b.make_terms(s3, wl.heisenberg_terms(wl.chain_bonds(L), 1.0)).path == "panel"
+    assert b.make_terms(s3, terms).path == "general"
     check(*run_both(L, 8, terms, seed=5, want_panel=False))
     s30 = b.make_sector(30, 2, 15, 2)  # P_1 of 15 sites: the general kernel
     assert b.make_terms(s30, wl.heisenberg_terms(wl.chain_bonds(30), np.linspace(0.5, 1.5, 30))).path == "general"

@@ -83,7 +83,7 @@ def test_nonfinite_input_gives_nan_and_error_word():
 
 def test_disorder_and_wide_last_subsystem_take_other_kernels():
     """Per-bond couplings (more classes than the panel kernels hold) and a last subsystem outside
-    8..10 sites leave the warp-panel kernel; the product still matches the oracle."""
+    8..10 sites leave the warp-panel kernel; the disordered product still matches the oracle."""
     rng = np.random.default_rng(4)
     L, N = 24, 10
     terms = wl.heisenberg_terms(wl.chain_bonds(L), rng.uniform(0.5, 1.5, L))
@@ -92,9 +92,9 @@ def test_disorder_and_wide_last_subsystem_take_other_kernels():
     assert t.path == "general"
     o = OracleSector(L, 2, N, partition=s.partition)
     check(s, t, terms, o, rng.uniform(-1, 1, o.dim))
-    s5 = b.make_sector(30, 2, 5, 5)  # subsystems of six sites
+    s5 = b.make_sector(30, 2, 5, 5)  # subsystems of six sites: the panel kernel with a tail of two
     t5 = b.make_terms(s5, j1j2_chain_terms(30))
-    assert t5.path == "general"
+    assert t5.path == "panel"
 
 
 @pytest.mark.slow
