@@ -466,7 +466,7 @@ def run_diff(args, world, rank, local, dist, torch):
                        "step": "y = H(theta) x, then dx and dtheta"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "traffic": None, "peak_source": peak_kind, "algorithmic_bytes_per_launch": alg_bytes,
-                         "kernel": {"panel": "k_panel", "panel_pb": "k_panel_pb", "panel_w": "k_panel_w"}.get(
+                         "kernel": {"panel": "k_panel", "panel_pb": "k_panel_pb", "panel_w": "k_panel_w", "panel_q": "k_panel_q"}.get(
                              op.compile(theta.detach()).path,
                              "k_matvec_q2_fx" if args.dtype == "f64" else "k_matvec_q2_f32x") + " + k_term_grads",
                          "main_kernels_ms_per_step": kern_ms / args.steps},
@@ -639,7 +639,8 @@ def main():
     path = t.path if args.nrhs == 1 else "general"
     general = (("k_matvec_q2_fx" if args.dtype == "f64" else "k_matvec_q2_f32x") if w.Q == 2 else
                ("k_matvec_qg_fx" if args.dtype == "f64" else "k_matvec_qg_f32x"))
-    kernel_name = {"panel": "k_panel", "panel_pb": "k_panel_pb", "panel_w": "k_panel_w", "cluster": "k_matvec_cl"}.get(path, general)
+    kernel_name = {"panel": "k_panel", "panel_pb": "k_panel_pb", "panel_w": "k_panel_w", "panel_q": "k_panel_q",
+                   "cluster": "k_matvec_cl"}.get(path, general)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
         barrier()

@@ -271,11 +271,11 @@ class Terms:
 
     @property
     def path(self) -> str:
-        """'panel', 'panel_pb', 'panel_w', 'general' or 'cluster': the product kernel used for one
-        right-hand side."""
+        """'panel', 'panel_pb', 'panel_w', 'panel_q', 'general' or 'cluster': the product kernel used
+        for one right-hand side."""
         v = ctypes.c_int()
         _check(_lib.dq_terms_path(self._h, ctypes.byref(v)))
-        return {1: "panel", 2: "cluster", 3: "panel_pb", 4: "panel_w"}.get(v.value, "general")
+        return {1: "panel", 2: "cluster", 3: "panel_pb", 4: "panel_w", 5: "panel_q"}.get(v.value, "general")
 
     def __del__(self):
         h = getattr(self, "_h", None)

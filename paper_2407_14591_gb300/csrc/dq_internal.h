@@ -236,6 +236,38 @@ struct PanelPB {
     const uint64_t* list;
 };
 
+// Plan of the boson panel product (Q > 2, two subsystems; dq_panel_q.cu): the panels of the
+// canonical order (rows sharing one P_0 pattern s0, contiguous by Lin's two tables, Sec. 3.3).
+// Everything that depends only on the row's P_1 pattern is tabulated once per pattern and read
+// by every panel of its particle-number block: the P_1 site functions, the hops inside P_1 (the
+// partner's local index and the amplitude entry, padded to one length per block with a zero
+// amplitude), and the local index of the partner row for every hop direction across the cut.
+constexpr int kPQMaxBits = 14;  // nb * L_1: at most 16384 P_1 patterns
+constexpr int kPQMaxN = 32;     // particle numbers of P_1 (plus one)
+constexpr int kPQMaxCut = 255;  // hop directions across the cut
+constexpr int kPQMaxList = 64;  // P_0 and cut entries of one panel
+struct PanelQ {
+    int Q, nb, L1, N, emin, nM, ncut;
+    uint32_t npanels;
+    const uint32_t* panel_s0;     // P_0 pattern of every panel, longest panels first
+    const uint64_t* panel_start;  // first index of every panel
+    uint32_t t1start[kPQMaxN + 1], t1len[kPQMaxN + 1];  // P_1 patterns per particle number
+    const long long* Mhop;        // [bonds][Q][Q]: -t sqrt((n_up + 1) n_dn) on the grid 2^emin; entry nM is 0
+    // per P_1 pattern (index t1start[n1] + local index c):
+    const long long* rdiag;       // the P_1 site functions
+    const uint32_t* p1ell;        // from p1base[n1], p1m[n1] slots of C entries: partner | Mhop entry << 16
+    uint32_t p1base[kPQMaxN + 1], p1m[kPQMaxN + 1];
+    const uint32_t* cutt;         // from cutbase[n1], ncut slots of C entries: partner local index |
+                                  // row part of the Mhop entry << 16 | (the hop is not allowed) << 31
+    uint32_t cutbase[kPQMaxN + 1];
+    const long long* pdiag;       // per panel: the constant plus the P_0 site functions
+    // per-panel sources: P_0 partners (start | Mhop entry << 40), then cut partners
+    // (start | cut direction << 40 | panel part of the Mhop entry << 48)
+    const uint32_t* list_off;
+    const uint32_t* list_hdr;     // bits 0-7: P_0 entries, 8-15: cut entries
+    const uint64_t* list;
+};
+
 // Host-side tables kept by a sector.
 struct HostTables {
     std::vector<uint64_t> Dq;  // (L+1) x (nmax_total+1), saturated at UINT64_MAX
@@ -271,6 +303,8 @@ struct dq_terms {
     bool panel_ok = false;     // the panel product applies (see PanelPlan)
     bool pb_ok = false;        // the per-bond panel product applies (PanelPB)
     bool pw_ok = false;        // the warp-panel product applies (three or more subsystems, PanelPlan)
+    bool pq_ok = false;        // the boson panel product applies (Q > 2, PanelQ)
+    dq::PanelQ pqp;
     dq::PanelPB pbp;
     bool cluster = false;      // cluster-merged form (App. C), dq_make_cluster_terms
     dq::DevTermsCL clv;
@@ -318,6 +352,13 @@ int build_panel_plan(const dq_sector* s, double C, bool uniform_lin,
                      const std::vector<std::pair<std::pair<int, int>, std::pair<double, double>>>& pairs, dq_terms* t);
 int launch_panel_matvec(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
 int launch_panel_w(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
+// boson panel product (dq_panel_q.cu): the plan from the compiled per-term coefficients (site
+// shifts and their [site][Q] functions, hop shifts and the [hop][Q][Q] amplitudes, all on the grid
+// 2^emin), and the launch
+int build_panel_q(const dq_sector* s, const std::vector<int>& site_sh, const std::vector<long long>& msite,
+                  const std::vector<int>& hop_sh, const std::vector<long long>& mhop, long long MC, int emin,
+                  int npair, dq_terms* t);
+int launch_panel_q(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
 int launch_panel_w_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,
                       void* stream);
 size_t panel_scratch_bytes(const dq_sector* s, int dtype);

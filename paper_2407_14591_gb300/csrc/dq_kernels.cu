@@ -444,6 +444,7 @@ int launch_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y,
     if (t->cluster) return launch_cluster_matvec(s, const_cast<dq_terms*>(t), x, y, dtype, nrhs, stream);
     if (t->panel_ok && nrhs == 1) return launch_panel_matvec(s, const_cast<dq_terms*>(t), x, y, dtype, stream);
     if (t->pw_ok && nrhs == 1) return launch_panel_w(s, const_cast<dq_terms*>(t), x, y, dtype, stream);
+    if (t->pq_ok && nrhs == 1) return launch_panel_q(s, const_cast<dq_terms*>(t), x, y, dtype, stream);
     if (t->pb_ok && nrhs == 1) return launch_panel_pb(s, const_cast<dq_terms*>(t), x, y, dtype, stream);
     if (dtype == DQ_F64) return launch_matvec_fx(s, const_cast<dq_terms*>(t), (const double*)x, (double*)y, nrhs, st);
     return launch_matvec_f32x(s, const_cast<dq_terms*>(t), (const float*)x, (float*)y, nrhs, st);

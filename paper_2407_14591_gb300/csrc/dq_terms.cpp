@@ -391,6 +391,13 @@ static int compile_qg(const dq_sector* s, const dq_term* terms, int n, dq_terms*
         if ((rc = upm(site_f, &v.Msite))) return rc;
         if ((rc = upm(pair_K, &v.Mpair))) return rc;
         if ((rc = upm(hop_amp, &v.Mhop))) return rc;
+        {
+            // the boson panel product takes the same integer coefficients
+            std::vector<long long> msite(site_f.size()), mhop(hop_amp.size());
+            for (size_t k = 0; k < site_f.size(); ++k) msite[k] = M(site_f[k]);
+            for (size_t k = 0; k < hop_amp.size(); ++k) mhop[k] = M(hop_amp[k]);
+            if ((rc = build_panel_q(s, site_sh, msite, hop_sh, mhop, v.MC, v.emin, v.npair, t))) return rc;
+        }
         // FP32 vectors: hop amplitudes with at most 24 bits (int32), the diagonal on a finer grid
         {
             double cmax_h = 0.0, cmax_d = std::fabs(C);
@@ -468,7 +475,7 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
 int dq_terms_path(const dq_terms* t, int* path) {
     clear_error();
     if (!t || !path) return set_error(DQ_EINVAL, "NULL argument");
-    *path = t->cluster ? 2 : (t->panel_ok ? 1 : (t->pw_ok ? 4 : (t->pb_ok ? 3 : 0)));
+    *path = t->cluster ? 2 : (t->panel_ok ? 1 : (t->pw_ok ? 4 : (t->pb_ok ? 3 : (t->pq_ok ? 5 : 0))));
     return DQ_OK;
 }
 

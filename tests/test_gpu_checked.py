@@ -26,8 +26,9 @@ rng = np.random.default_rng(5)
 cases = []
 J = rng.uniform(0.5, 1.5, 14); h = rng.uniform(-3, 3, 14)
 cases.append((14, 2, 7, 3, wl.heisenberg_terms(wl.chain_bonds(14), J, 1.0) + wl.field_terms(h), 3))
-cases.append((10, 4, 12, 2, [("HOP", i, j, 1.0) for i, j in wl.chain_bonds(10)]
-              + [("U", i, -1, float(u)) for i, u in enumerate(rng.uniform(2, 6, 10))], 1))
+bh = [("HOP", i, j, 1.0) for i, j in wl.chain_bonds(10)] + [("U", i, -1, float(u)) for i, u in enumerate(rng.uniform(2, 6, 10))]
+cases.append((10, 4, 12, 2, bh, 2))  # two right-hand sides: the general boson kernel
+cases.append((10, 4, 12, 2, bh, 1))  # one: the boson panel kernel
 for L, Q, N, n_sub, terms, nrhs in cases:
     s = b.make_sector(L, Q, N, n_sub); t = b.make_terms(s, terms)
     o = OracleSector(L, Q, N, partition=s.partition)
