@@ -178,9 +178,8 @@ int dq_make_terms(const dq_sector* s, const dq_term* terms, int n_terms, dq_term
  * the boson panel kernel: Q > 2, two subsystems, one-word states, P_1 of at most 14 bits
  * (Nbits * L_1 <= 14) and P_0 of at most 24, no n_i n_j pair terms, D < 2^40, at most 31 hop
  * bonds and 4096 hop amplitude entries (bonds x Q x Q), 64 P_0 and cut hops per panel; any
- * coefficient per
- * hop bond and any site function (the per-term form's integer coefficients, so it gives the
- * general kernel's y). */
+ * coefficient per hop bond and any site function (the per-term form's integer coefficients, so
+ * it gives the general kernel's y). */
 int dq_terms_path(const dq_terms* t, int* path);
 
 /* Compile terms in the cluster-merged form of App. C instead: the terms are grouped into clusters
