@@ -230,9 +230,10 @@ int dq_matvec(const dq_sector* s, const dq_terms* t, const void* x, void* y, int
  * terms.
  * The scratch (a fixed-point copy of x and a small header) lives in a static device array of
  * 64 MiB that every GPU loading this library reserves until the process exits. Hence the limit:
- * D <= 8,388,568 for DQ_F64 and D <= 16,777,144 for DQ_F32; larger sectors return DQ_ERANGE with
- * the limit in dq_last_error(). Only terms on the panel paths (dq_terms_path 1 or 4) are
- * served; others return DQ_EINVAL. The first call on a device does a one-time set-up: it looks up the
+ * D <= 8,388,568 for DQ_F64 and D <= 16,777,144 for DQ_F32 (8,388,568 for both on the boson panel
+ * path, which keeps x as 64-bit words); larger sectors return DQ_ERANGE with the limit in
+ * dq_last_error(). Only terms on the panel paths (dq_terms_path 1, 4 or 5) are served; others
+ * return DQ_EINVAL. The first call on a device does a one-time set-up: it looks up the
  * array's device address (cudaGetSymbolAddress) and caches it. With CUDA's default lazy module
  * loading, that lookup is also when the runtime loads the code module holding the array, so the
  * 64 MiB are taken from the device at that first call, not when the library is loaded: make the

@@ -359,6 +359,9 @@ int build_panel_q(const dq_sector* s, const std::vector<int>& site_sh, const std
                   const std::vector<int>& hop_sh, const std::vector<long long>& mhop, long long MC, int emin,
                   int npair, dq_terms* t);
 int launch_panel_q(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream);
+// the same with caller-provided scratch of panel_scratch_bytes(s, DQ_F64) bytes (both dtypes)
+int launch_panel_q_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,
+                      void* stream);
 int launch_panel_w_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,
                       void* stream);
 size_t panel_scratch_bytes(const dq_sector* s, int dtype);

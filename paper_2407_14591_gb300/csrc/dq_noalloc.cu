@@ -2,7 +2,7 @@
 // for callers that must not allocate device memory while they run (see include/dq.h).
 //
 // The scratch holds the workspace header and the fixed-point copy of x that the panel kernels
-// read (dq_panel.cu, dq_panel_w.cu). The array is static: it is reserved when the code module that holds it
+// read (dq_panel.cu, dq_panel_w.cu, dq_panel_q.cu). The array is static: it is reserved when the code module that holds it
 // is loaded on a GPU and stays reserved until the process exits. Under CUDA's default lazy
 // module loading this file's module (it has no kernels of its own) is loaded by the first
 // cudaGetSymbolAddress on each device, i.e. inside the first dq_matvec_noalloc call there, which
@@ -55,9 +55,10 @@ extern "C" int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const vo
     if (t->sector != s) return set_error(DQ_EINVAL, "terms were compiled for another sector");
     if (!s->has_device) return set_error(DQ_ECUDA, "no CUDA device: the sector has host tables only");
     if (dtype != DQ_F64 && dtype != DQ_F32) return set_error(DQ_EINVAL, "dtype must be DQ_F64 or DQ_F32");
-    if (!t->panel_ok && !t->pw_ok)
-        return set_error(DQ_EINVAL, "dq_matvec_noalloc serves only terms on the panel paths (dq_terms_path 1 or 4)");
-    const size_t need = panel_scratch_bytes(s, dtype);
+    if (!t->panel_ok && !t->pw_ok && !t->pq_ok)
+        return set_error(DQ_EINVAL, "dq_matvec_noalloc serves only terms on the panel paths (dq_terms_path 1, 4 or 5)");
+    // the boson panel kernel keeps x as split 64-bit words for both dtypes
+    const size_t need = panel_scratch_bytes(s, t->pq_ok && !t->panel_ok && !t->pw_ok ? DQ_F64 : dtype);
     if (need > kNoAllocScratchBytes)
         return set_error(DQ_ERANGE,
                          "sector too large for the static scratch: needs %zu bytes, the limit is %zu bytes "
@@ -72,7 +73,8 @@ extern "C" int dq_matvec_noalloc(const dq_sector* s, const dq_terms* t, const vo
     int rc = noalloc_scratch(&ws);
     if (rc) return rc;
     int e = t->panel_ok ? launch_panel_matvec_ws(s, t, x, y, dtype, ws, stream)
-                        : launch_panel_w_ws(s, t, x, y, dtype, ws, stream);
+            : t->pw_ok  ? launch_panel_w_ws(s, t, x, y, dtype, ws, stream)
+                        : launch_panel_q_ws(s, t, x, y, dtype, ws, stream);
     if (e) return set_error(DQ_ECUDA, "matvec_noalloc launch: %s", cudaGetErrorString((cudaError_t)e));
     return DQ_OK;
 }

@@ -394,6 +394,13 @@ static int run_panel_q(const dq_sector* s, const dq_terms* t, const T* x, T* y, 
     return (int)cudaGetLastError();
 }
 
+int launch_panel_q_ws(const dq_sector* s, const dq_terms* t, const void* x, void* y, int dtype, void* ws,
+                      void* stream) {
+    cudaStream_t st = (cudaStream_t)stream;
+    if (dtype == DQ_F64) return run_panel_q<double>(s, t, (const double*)x, (double*)y, ws, st);
+    return run_panel_q<float>(s, t, (const float*)x, (float*)y, ws, st);
+}
+
 int launch_panel_q(const dq_sector* s, dq_terms* t, const void* x, void* y, int dtype, void* stream) {
     const size_t need = panel_scratch_bytes(s, DQ_F64);  // split 64-bit x for both dtypes
     if (t->scratch_bytes < need) {
@@ -404,9 +411,7 @@ int launch_panel_q(const dq_sector* s, dq_terms* t, const void* x, void* y, int 
         if (e != cudaSuccess) return (int)e;
         t->scratch_bytes = need;
     }
-    cudaStream_t st = (cudaStream_t)stream;
-    if (dtype == DQ_F64) return run_panel_q<double>(s, t, (const double*)x, (double*)y, t->scratch, st);
-    return run_panel_q<float>(s, t, (const float*)x, (float*)y, t->scratch, st);
+    return launch_panel_q_ws(s, t, x, y, dtype, t->scratch, stream);
 }
 
 }  // namespace dq

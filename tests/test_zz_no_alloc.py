@@ -51,6 +51,24 @@ def test_noalloc_matches_matvec_on_two_calls(lat, path):
     assert torch.linalg.norm(out32.double() - ref32.double()) <= 1e-5 * torch.linalg.norm(ref32.double())
 
 
+def test_noalloc_boson_panel_path():
+    """The boson panel path (Q = 4, two subsystems; D = 44,803) against dq_matvec, FP64 and FP32."""
+    rng = np.random.default_rng(4)
+    L = 10
+    terms = [("HOP", i, j, 1.0) for i, j in wl.chain_bonds(L)] + [("U", i, -1, float(u)) for i, u in
+                                                                   enumerate(rng.uniform(2, 6, L))]
+    s = b.make_sector(L, 4, L, 2)
+    t = b.make_terms(s, terms)
+    assert t.path == "panel_q"
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        x = torch.from_numpy(rng.uniform(-1, 1, s.dim)).to("cuda", dt)
+        ref = b.matvec(s, t, x, torch.empty_like(x))
+        out = b.matvec_noalloc(s, t, x, torch.full_like(x, float("nan")))
+        torch.cuda.synchronize()
+        s.check_device()
+        assert torch.max(torch.abs(out.double() - ref.double())).item() <= tol * torch.max(torch.abs(ref.double())).item()
+
+
 def test_noalloc_rejects_too_large_and_off_path():
     s = b.make_sector(26, 2, 13, 2)  # D = 10,400,600 > 8,388,568 (FP64 limit)
     t = b.make_terms(s, wl.heisenberg_terms(wl.chain_bonds(26), 1.0))
@@ -60,8 +78,11 @@ def test_noalloc_rejects_too_large_and_off_path():
     rc = lib.dq_matvec_noalloc(s.handle, t.handle, dummy, ctypes.c_void_p(0x10000000000), b.DQ_F64, _stream())
     assert rc == b.DQ_ERANGE
     assert b"8388568" in lib.dq_last_error()
-    s2 = b.make_sector(12, 2, 6, 3)  # three subsystems: general path only
-    t2 = b.make_terms(s2, wl.heisenberg_terms(wl.chain_bonds(12), 1.0))
+    # per-bond couplings with three subsystems: the general kernel, which the call does not serve
+    # (checked before the call: the call must return before it could launch anything)
+    s2 = b.make_sector(12, 2, 6, 3)
+    t2 = b.make_terms(s2, wl.heisenberg_terms(wl.chain_bonds(12), np.linspace(0.5, 1.5, 12)))
+    assert t2.path == "general"
     rc = lib.dq_matvec_noalloc(s2.handle, t2.handle, dummy, ctypes.c_void_p(0x10000000000), b.DQ_F64, _stream())
     assert rc == b.DQ_EINVAL
 
