@@ -1,7 +1,7 @@
 """The boson panel product (Q > 2, two subsystems; site functions and hops with any coefficient per
 site and per bond) against the oracle: FP64 (max-relative 1e-12) and FP32 vectors (relative L2
 1e-5 against the oracle applied to the rounded x), on Bose-Hubbard chains and a ladder with Q = 3,
-4 and 8, disordered hops and fields, extreme particle numbers (empty, one particle, full), a
+4, 5 and 8, disordered hops and fields, extreme particle numbers (empty, one particle, full), a
 non-finite input, bit-for-bit agreement with the general kernel on FP64 vectors, and the
 operators it leaves to the general kernel (n_i n_j pairs, more than two subsystems). Workload 3 at
 full size is in the full-size parity test.
